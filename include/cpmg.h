@@ -1,0 +1,208 @@
+/*
+ * cpmg.h — C ABI of libcpmg, a GB300 (sm_103a) implementation of the data-parallel
+ * hot path of the adaptive algebraic multigrid method for low-rank canonical (CP)
+ * tensor decomposition of De Sterck and Miller.
+ *
+ * The problem (Eq. CPfunctional): given a dense N-way tensor Z of size
+ * I_1 x ... x I_N and a rank R, find factor matrices A^(1..N) (A^(n) is I_n x R)
+ * minimizing f = 1/2 || Z - [[A^(1), ..., A^(N)]] ||^2.
+ *
+ * Conventions used by every call
+ * ------------------------------
+ *  - Tensors are dense and column-major: element (i_1, ..., i_N) (0-based) sits at
+ *    offset i_1 + I_1 (i_2 + I_2 (i_3 + ...)).  This is the order under which the
+ *    mode-n matricization of Section 2 (earlier modes fastest) is a plain reshape.
+ *  - Factor matrices are float64, column-major I_n x R (element (i, r) at i + I_n r).
+ *  - Memory space: `cpmg_tensor.mem` says whether Z, and every factor / TFM array
+ *    passed with it in the same call, are device pointers (CPMG_MEM_DEVICE, on the
+ *    context's device) or host pointers (CPMG_MEM_HOST; the library copies them to
+ *    the device and the results back inside the call).
+ *  - Ownership: the caller owns Z, the factor arrays and the TFM arrays.  Z is only
+ *    read and must stay valid until the call returns.  The library owns contexts,
+ *    hierarchies and all workspace memory (allocated with cudaMalloc on the
+ *    context's device; released by cpmg_destroy / cpmg_hier_free).
+ *  - Streams: work is issued on the stream given to cpmg_create (or
+ *    cpmg_set_stream).  Every call below is synchronous with respect to the host:
+ *    it returns after its results are in the caller's buffers.
+ *  - Errors: every int-returning call returns a cpmg_status.  No call throws or
+ *    aborts; a CUDA error is reported as CPMG_CUDA_ERROR and leaves the context
+ *    usable only if the CUDA context itself is still usable.
+ *  - Limits: 2 <= N <= CPMG_MAX_MODES, 1 <= R <= CPMG_MAX_RANK, every I_n >= 1.
+ *
+ * Precision: matricized-tensor-times-Khatri-Rao products (MTTKRP) and the
+ * restriction (TTM) read Z in its own type.  Grams, Hadamard products, R x R
+ * solves, f and g are always float64.  See cpmg_opts.precision.
+ */
+#ifndef CPMG_H
+#define CPMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPMG_MAX_MODES 8
+#define CPMG_MAX_RANK 16
+#define CPMG_MAX_TEST_BLOCKS 4
+
+typedef enum {
+  CPMG_OK = 0,
+  CPMG_INVALID_ARG = 1,    /* bad shape, rank, dtype, pointer or option              */
+  CPMG_OUT_OF_BUDGET = 2,  /* the call would exceed the context's HBM budget         */
+  CPMG_NOT_CONVERGED = 3,  /* iteration cap reached; outputs hold the last iterate   */
+  CPMG_NUMERIC = 4,        /* NaN/Inf met in f, g or the factors                     */
+  CPMG_TIMEOUT = 5,        /* a bounded device-side wait expired                     */
+  CPMG_CUDA_ERROR = 6,     /* a CUDA runtime call failed                             */
+  CPMG_PENDING = 7,        /* server: request not finished yet                       */
+  CPMG_CANCELLED = 8,
+  CPMG_UNSUPPORTED = 9     /* valid request this build does not handle              */
+} cpmg_status;
+
+typedef enum { CPMG_F32 = 0, CPMG_F64 = 1 } cpmg_dtype;
+typedef enum { CPMG_MEM_DEVICE = 0, CPMG_MEM_HOST = 1 } cpmg_mem;
+
+/* Arithmetic of the MTTKRP inside relaxation sweeps. */
+typedef enum {
+  CPMG_PREC_FP32 = 0,   /* float products, float accumulation (fastest; g floor ~1e-7 relative) */
+  CPMG_PREC_FP64 = 1,   /* float64 products and accumulation: the plain FP64 path               */
+  CPMG_PREC_MIXED = 2,  /* FP32 sweeps, then float64-accurate sweeps once g nears the FP32 floor */
+  CPMG_PREC_DF = 3      /* float64-accurate sweeps from the start (pairs of floats)              */
+} cpmg_precision;
+
+typedef struct cpmg_ctx cpmg_ctx;    /* device, stream, workspaces, statistics            */
+typedef struct cpmg_hier cpmg_hier;  /* a multigrid hierarchy: coarse tensors and operators */
+
+typedef struct {
+  int N;                             /* number of modes                                      */
+  int64_t dims[CPMG_MAX_MODES];      /* I_1..I_N                                             */
+  int dtype;                         /* cpmg_dtype                                           */
+  int mem;                           /* cpmg_mem of data (and of the factor arrays)          */
+  const void* data;                  /* column-major tensor                                  */
+} cpmg_tensor;
+
+/* Options.  cpmg_opts_default() fills the paper's parameters (Table tab:params and
+ * Section 6.1): setup nu1 = nu2 = 5, nu_c = 100, n_t = 2; solve nu1 = nu2 = 1,
+ * nu_c = 50; ten Gauss-Seidel sweeps; tol = 1e-10; at most 500 multilevel cycles,
+ * 1e4 ALS iterations and 5 setup cycles; stagnation eps = 0.1. */
+typedef struct {
+  int precision;                     /* cpmg_precision                                       */
+  double tol;                        /* stop when g < tol (Eq. gradConv, Eq. stopcrit)        */
+  int max_cycles;                    /* multilevel cycles, setup + solve                      */
+  int max_als_iters;
+  int nu1_setup, nu2_setup, nuc_setup;
+  int nu1, nu2, nuc;
+  int n_t;                           /* test blocks (TFMs), <= CPMG_MAX_TEST_BLOCKS           */
+  int max_setup_cycles;
+  double stag_eps;
+  int gs_sweeps;                     /* Gauss-Seidel sweeps in BNGS (Section 5.2)             */
+  int64_t coarsest[CPMG_MAX_MODES];  /* I_{n,coarsest}: mode n is coarsened while I_n > this  */
+  int als_fallback;                  /* 1: plain ALS after a second solve-phase stagnation    */
+                                     /*    (an addition; the paper stops after one rebuild)   */
+  double mixed_switch;               /* MIXED: switch to float64-accurate sweeps when
+                                        g < mixed_switch * (FP32 floor estimate); <= 0: 64     */
+  int check_every;                   /* cp_als_sweep: evaluate g every k sweeps (0 = never)   */
+} cpmg_opts;
+
+typedef struct {
+  double f;                          /* 1/2 ||Z - [[A]]||^2, float64, at the returned factors */
+  double g;                          /* Eq. gradConv at the returned factors                   */
+  int iters_setup;                   /* setup (CP-AMG-mult) cycles                             */
+  int iters_solve;                   /* solve (CP-FAS) cycles                                  */
+  int iters_als;                     /* ALS iterations (cp_als_sweep, or the fallback)         */
+  int levels;
+  int restarted;                     /* solve-phase rebuild happened                           */
+  int refine_sweeps;                 /* sweeps done with float64-accurate MTTKRP               */
+  int status;
+  double seconds;                    /* wall time of the call                                  */
+} cpmg_result;
+
+/* ---- context ---------------------------------------------------------------------- */
+void cpmg_opts_default(cpmg_opts* opts);
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  hbm_budget_bytes caps the
+ * workspace and hierarchy memory the context may allocate (0 = no cap).
+ * Returns CPMG_INVALID_ARG for a null out-pointer, CPMG_CUDA_ERROR if the device
+ * cannot be selected. */
+int cpmg_create(cpmg_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
+void cpmg_destroy(cpmg_ctx* ctx);
+int cpmg_set_stream(cpmg_ctx* ctx, void* cuda_stream);
+const char* cpmg_status_str(int status);
+/* Bytes of device memory the context currently holds. */
+size_t cpmg_bytes_in_use(const cpmg_ctx* ctx);
+
+/* ---- kernels exposed for verification (device pointers only) ------------------------ */
+
+/* M = Z_(n) Phi^(n), the MTTKRP of Eq. fineeq1 / Eq. gradEqn with
+ * Phi^(n) = A^(N) (.) ... (.) A^(n+1) (.) A^(n-1) (.) ... (.) A^(1) (Eq. Phi).
+ * mode is 0-based.  A[m] are device float64 I_m x R; M is a device float64
+ * I_n x R output.  precision: CPMG_PREC_FP32, CPMG_PREC_FP64 or CPMG_PREC_DF. */
+int cpmg_mttkrp(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, const double* const* A, int mode,
+                int precision, double* M);
+
+/* Y = Z x_{n : Rhat[n] != NULL} Rhat^(n), the restriction of Eq. ctensor_transformed applied
+ * one mode at a time in increasing n.  Rhat[n] is a device float64 Ic_n x I_n column-major
+ * matrix or NULL (mode not coarsened).  Y is a device tensor of Z's dtype with the coarse
+ * sizes, column-major.  tensor_cores: 0 = FP32/FP64 CUDA-core GEMM, 1 = tcgen05 (float Z). */
+int cpmg_ttm(cpmg_ctx* ctx, const cpmg_tensor* Z, const double* const* Rhat, const int64_t* Ic,
+             int tensor_cores, void* Y);
+
+/* f = 1/2 ||Z - [[A]]||^2 (Eq. CPfunctional, element by element in float64) and
+ * g (Eq. gradConv, with float64-accurate MTTKRPs).  Either output may be NULL. */
+int cpmg_eval_fg(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, const double* const* A,
+                 double* f, double* g);
+
+/* ---- the solver calls --------------------------------------------------------------- */
+
+/* ALS (Section 3): up to nsweeps iterations of block nonlinear Gauss-Seidel over modes
+ * n = 1..N, each A^(n) <- Z_(n) Phi^(n) (Gamma^(n))^+ with Gamma^(n) the Hadamard product
+ * of the other modes' Grams (Eq. Gamma), followed by the normalization of Eq. ALSnorm;
+ * the components are sorted by decreasing lambda at the end (end of Section 3).
+ * If opts->check_every > 0 the call stops once g < opts->tol.
+ * A[0..N-1]: factor arrays, read as the start and overwritten with the result. */
+int cp_als_sweep(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A, int nsweeps,
+                 const cpmg_opts* opts, cpmg_result* result);
+
+/* Setup phase (Section 4.5 Algorithm 1 CP-AMG-mult V-cycles, with the stagnation rule of
+ * Eq. stagnation and the cycle cap of Section 6.1).  A_boot: the boot factor matrices
+ * (BFMs), in/out.  A_test: n_t * N arrays, block t mode n at A_test[t*N + n], the test
+ * factor matrices (TFMs), in/out (the updated fine-level TFMs are returned).  *out
+ * receives a new hierarchy (free with cpmg_hier_free). */
+int mg_setup(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A_boot,
+             double* const* A_test, const cpmg_opts* opts, cpmg_hier** out, cpmg_result* result);
+
+/* Solve phase (Section 5.3 Algorithm 2 CP-FAS V-cycles with F = 0 on the finest level)
+ * until g < tol or the cycle cap, with the one-time rebuild of Section 6.1 (which uses
+ * the hierarchy's stored TFMs) and, if opts->als_fallback, plain ALS after a second
+ * stagnation.  A: in/out factors.  Z must be the tensor the hierarchy was built from. */
+int mg_fas_solve(cpmg_ctx* ctx, cpmg_hier* hier, const cpmg_tensor* Z, double* const* A,
+                 const cpmg_opts* opts, cpmg_result* result);
+void cpmg_hier_free(cpmg_hier* hier);
+int cpmg_hier_levels(const cpmg_hier* hier);
+/* Copy level `level`'s tensor dims (and, if Y != NULL, the device tensor itself, in the
+ * level's dtype) and its R-hat operators (host float64 column-major arrays, NULL to skip). */
+int cpmg_hier_level_info(const cpmg_hier* hier, int level, int64_t* dims, int* coarsened,
+                         void* Y_device, double* const* Rhat_host);
+
+/* The "Multilevel" solver of Section 6.1 in one call: mg_setup then mg_fas_solve.
+ * Accepts host buffers (Z->mem == CPMG_MEM_HOST): the copies are part of the call. */
+int cpmg_decompose(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A,
+                   double* const* A_test, const cpmg_opts* opts, cpmg_result* result);
+
+/* Per-kernel timing: when enabled, each launch of the finest-level MTTKRP main kernel is
+ * bracketed by CUDA events on the context's stream; the statistics accumulate until reset.
+ * kind: 0 = FP32 launches, 1 = float64-accurate (pairs of floats), 2 = FP64.  bytes_per_launch
+ * is the algorithmic traffic: sizeof(z) * prod(I) + 4 R sum_n I_n. */
+int cpmg_profile_enable(cpmg_ctx* ctx, int enable);
+int cpmg_profile_read(cpmg_ctx* ctx, int kind, double* total_ms, int64_t* launches,
+                      double* bytes_per_launch);
+int cpmg_profile_reset(cpmg_ctx* ctx);
+/* Number of kernel launches issued by this context since creation (all kinds). */
+int64_t cpmg_launch_count(const cpmg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPMG_H */

@@ -25,3 +25,16 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def cpmg_ctx():
+    """A libcpmg context on cuda:0 (GPU tests only); builds the library if needed."""
+    import torch
+    from paper_1111_6091_gb300 import build, cpmg
+    build.build()
+    torch.cuda.set_device(0)
+    c = cpmg.Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()

@@ -1,0 +1,158 @@
+"""GPU parity of the solver calls (cp_als_sweep, mg_setup, mg_fas_solve, cpmg_decompose)
+against the FP64 oracle, from identical starts."""
+import numpy as np
+import pytest
+
+from oracle import tensor as T, als as ALS, multigrid as MG, align
+from paper_1111_6091_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(cpmg, arrs):
+    return [cpmg.colmajor(a) for a in arrs]
+
+
+def host(cpmg, ts):
+    return [cpmg.to_numpy(t) for t in ts]
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_one_als_sweep_matches_oracle(cpmg_ctx, dt):
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((24, 20, 18), 4, congruence=0.5, eta_homo=0.01, dtype=dt, seed=1)
+    Z64 = p.Z.astype(np.float64)
+    ref = ALS.sort_components(ALS.als_sweep(Z64, p.A0))
+    for prec, tol in ((cpmg.PREC_FP64, 1e-10), (cpmg.PREC_DF, 1e-9), (cpmg.PREC_FP32, 2e-4)):
+        if prec == cpmg.PREC_DF and dt == np.float64:
+            continue
+        A = dev(cpmg, p.A0)
+        cpmg.cp_als_sweep(cpmg_ctx, cpmg.colmajor(p.Z), A, 1, precision=prec, check_every=0)
+        for a, b in zip(host(cpmg, A), ref):
+            assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(b)), prec
+
+
+def test_als_exact_recovery_20cubed(cpmg_ctx):
+    """Exact rank-3 20^3 tensor (float64): f -> 0 and factor error <= 1e-10 against the truth,
+    and the same iterate count as the oracle (+-1)."""
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((20, 20, 20), 3, dtype=np.float64, seed=0)
+    for prec in (cpmg.PREC_FP64, cpmg.PREC_MIXED):
+        A = dev(cpmg, p.A0)
+        r = cpmg.cp_als_sweep(cpmg_ctx, cpmg.colmajor(p.Z), A, 10000, precision=prec, tol=1e-10, check_every=1)
+        got = host(cpmg, A)
+        assert r["status"] == cpmg.OK
+        assert T.g_value(p.Z, got) < 1e-10
+        assert align.factor_error(p.truth, got) <= 1e-10
+        assert r["f"] <= 1e-16 * np.sum(p.Z ** 2)
+    _, it = ALS.als(p.Z, p.A0, 10000, tol=1e-10, g_fn=T.g_value)
+    A = dev(cpmg, p.A0)
+    r = cpmg.cp_als_sweep(cpmg_ctx, cpmg.colmajor(p.Z), A, 10000, precision=cpmg.PREC_FP64, tol=1e-10, check_every=1)
+    assert abs(r["iters_als"] - it) <= 1
+
+
+def test_als_f_monotone(cpmg_ctx):
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((30, 25, 20), 4, congruence=0.8, eta_homo=0.05, dtype=np.float32, seed=2)
+    A = dev(cpmg, p.A0)
+    fprev = np.inf
+    for _ in range(20):
+        r = cpmg.cp_als_sweep(cpmg_ctx, cpmg.colmajor(p.Z), A, 1, precision=cpmg.PREC_DF, check_every=0)
+        assert r["f"] <= fprev * (1 + 1e-10)
+        fprev = r["f"]
+
+
+def test_setup_cycle_matches_oracle(cpmg_ctx):
+    """One CP-AMG-mult cycle (float64 arithmetic): the boot factors, the updated TFMs and the
+    level-0 operators R-hat agree with the oracle's."""
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((20, 20, 20), 3, dtype=np.float64, seed=0)
+    o = MG.Options(coarsest=(10, 10, 10), max_setup_cycles=1)
+    ref = MG.mg_setup(p.Z, p.A0, p.tfms, o)
+    A = dev(cpmg, p.A0)
+    tf = [dev(cpmg, b) for b in p.tfms]
+    h, r = cpmg.mg_setup(cpmg_ctx, cpmg.colmajor(p.Z), A, tf, precision=cpmg.PREC_FP64, max_setup_cycles=1,
+                         coarsest=(10, 10, 10))
+    assert r["levels"] == len(ref.levels) == 2
+    for a, b in zip(host(cpmg, A), ref.A):
+        assert np.max(np.abs(a - b)) <= 1e-8 * np.max(np.abs(b))
+    for blk_g, blk_r in zip(tf, ref.tfms):
+        for a, b in zip(host(cpmg, blk_g), blk_r):
+            assert np.max(np.abs(a - b)) <= 1e-8 * np.max(np.abs(b))
+    Rh = h.rhat(0, 3)
+    for n in range(3):
+        assert np.allclose(Rh[n], ref.levels[0].Rhat[n], rtol=1e-8, atol=1e-10)
+    Y, shape, co = h.level_tensor(1, 3, __import__("torch").float64)
+    assert shape == (10, 10, 10)
+    assert np.allclose(cpmg.to_numpy(Y), ref.levels[1].Z, rtol=1e-8, atol=1e-8 * np.max(np.abs(ref.levels[1].Z)))
+    h.free()
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_two_level_multilevel_20cubed(cpmg_ctx, prec):
+    """The float64 20^3 rank-3 configuration: two-level multilevel solve to g < 1e-10, factor
+    error <= 1e-10 against the exact factors, same cycle counts as the oracle."""
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((20, 20, 20), 3, dtype=np.float64, seed=0)
+    ref = MG.multilevel(p.Z, p.A0, p.tfms, MG.Options(coarsest=(10, 10, 10), tol=1e-10))
+    A = dev(cpmg, p.A0)
+    tf = [dev(cpmg, b) for b in p.tfms]
+    r = cpmg.cpmg_decompose(cpmg_ctx, cpmg.colmajor(p.Z), A, tf, precision=getattr(cpmg, "PREC_" + prec),
+                            tol=1e-10, coarsest=(10, 10, 10))
+    got = host(cpmg, A)
+    assert r["status"] == cpmg.OK and r["levels"] == 2
+    assert T.g_value(p.Z, got) < 1e-10
+    assert align.factor_error(p.truth, got) <= 1e-10
+    assert align.factor_error(ref.A, got) <= 1e-10
+    if prec == "FP64":
+        assert r["iters_setup"] == ref.setup_cycles and r["iters_solve"] == ref.solve_cycles
+
+
+def test_fas_solve_from_setup_matches_oracle(cpmg_ctx):
+    """mg_setup then mg_fas_solve as two calls on a 3-level float64 problem (coarsest 8)."""
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((32, 30, 28), 3, congruence=0.5, eta_homo=0.001, dtype=np.float64, seed=4)
+    o = MG.Options(coarsest=(8, 8, 8), tol=1e-9)
+    ref = MG.multilevel(p.Z, p.A0, p.tfms, o)
+    A = dev(cpmg, p.A0)
+    tf = [dev(cpmg, b) for b in p.tfms]
+    h, r1 = cpmg.mg_setup(cpmg_ctx, cpmg.colmajor(p.Z), A, tf, precision=cpmg.PREC_FP64, tol=1e-9,
+                          coarsest=(8, 8, 8))
+    r2 = cpmg.mg_fas_solve(cpmg_ctx, h, cpmg.colmajor(p.Z), A, precision=cpmg.PREC_FP64, tol=1e-9,
+                           coarsest=(8, 8, 8))
+    h.free()
+    got = host(cpmg, A)
+    assert r1["levels"] == len(ref.levels)
+    assert r2["g"] < 1e-9 and ref.converged
+    assert T.g_value(p.Z, got) < 1e-9
+    assert align.factor_error(ref.A, got) <= 1e-7
+
+
+def test_invalid_arguments(cpmg_ctx):
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    Z = torch.zeros((4, 5, 6), dtype=torch.float32, device="cuda")
+    A = [torch.zeros((2, I), dtype=torch.float64, device="cuda") for I in (6, 5, 4)]
+    with pytest.raises(cpmg.CpmgError) as e:
+        cpmg.cp_als_sweep(cpmg_ctx, Z, A, 1, precision=7)
+    assert e.value.status == cpmg.INVALID_ARG
+    A17 = [torch.zeros((17, I), dtype=torch.float64, device="cuda") for I in (6, 5, 4)]
+    with pytest.raises(cpmg.CpmgError):
+        cpmg.cp_als_sweep(cpmg_ctx, Z, A17, 1)
+    Z1 = torch.zeros((4,), dtype=torch.float32, device="cuda")
+    with pytest.raises(cpmg.CpmgError):
+        cpmg.cp_als_sweep(cpmg_ctx, Z1, [torch.zeros((2, 4), dtype=torch.float64, device="cuda")], 1)
+
+
+def test_host_buffers_roundtrip(cpmg_ctx):
+    """cpmg_decompose with host (pinned) buffers equals the device-buffer call bitwise."""
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((20, 20, 20), 3, dtype=np.float64, seed=0)
+    kw = dict(precision=cpmg.PREC_FP64, tol=1e-10, coarsest=(10, 10, 10))
+    A = dev(cpmg, p.A0)
+    cpmg.cpmg_decompose(cpmg_ctx, cpmg.colmajor(p.Z), A, [dev(cpmg, b) for b in p.tfms], **kw)
+    Ah = [cpmg.colmajor(a, device="cpu", pin=True) for a in p.A0]
+    tfh = [[cpmg.colmajor(a, device="cpu", pin=True) for a in b] for b in p.tfms]
+    cpmg.cpmg_decompose(cpmg_ctx, cpmg.colmajor(p.Z, device="cpu", pin=True), Ah, tfh, **kw)
+    for a, b in zip(host(cpmg, A), host(cpmg, Ah)):
+        assert np.array_equal(a, b)
