@@ -16,8 +16,11 @@ Readings of points the paper leaves open (all listed in the design notes):
   1-based points), coarse label i/2; an odd fine point i interpolates from
   coarse labels (i-1)/2 and (i+1)/2, or only (i-1)/2 when i+1 = I_n.
 * LS weights: w = ||A_t^(n)||_F^2 / ||G^(n)||_F^2 with G evaluated for that block
-  on the current level tensor at the block's current (relaxed) factors; when
-  ||G|| = 0, or the ratio exceeds 1e30, w = 1e30.
+  on the current level tensor at the block's current (relaxed) factors.  A gradient
+  at the rounding level of the arithmetic, ||G^(n)|| <= 1e-12 ||A^(n) Gamma^(n)||,
+  counts as zero (after an ALS iteration the last-updated mode's gradient is zero in
+  exact arithmetic, and its float value is noise); a zero gradient, or a ratio
+  above 1e30, gives w = 1e30, so such blocks weigh equally.
 * singular LS normal equations: if the 2x2 normal matrix has condition number
   above 1e12 (or is zero), the row gets weights (1/2, 1/2); a one-point stencil
   with a zero normal equation gets weight 1.
@@ -40,11 +43,12 @@ from __future__ import annotations
 import dataclasses
 import numpy as np
 
-from .tensor import as64, ttm_modes, gradient, fas_operator, g_value
+from .tensor import as64, ttm_modes, gradient, fas_operator, g_value, gamma, mttkrp
 from .als import als, bngs_sweep
 
 W_CAP = 1e30
 COND_MAX = 1e12
+G_ZERO_REL = 1e-12
 
 
 @dataclasses.dataclass
@@ -98,11 +102,15 @@ def stencil(i, I):
 
 # ---------------------------------------------------------------- Section 4.4
 def block_weight(Z, block, n):
-    """Eq. interpweights: ||A_t^(n)||^2 / ||G^(n)||^2 for one block of factor matrices."""
+    """Eq. interpweights: ||A_t^(n)||^2 / ||G^(n)||^2 for one block of factor matrices, with
+    G^(n) = A^(n) Gamma^(n) - Z_(n) Phi^(n) (Eq. gradEqn) treated as zero below the
+    rounding level G_ZERO_REL * ||A^(n) Gamma^(n)||."""
     a2 = float(np.sum(block[n] * block[n]))
-    G = gradient(Z, block, n)
+    AG = block[n] @ gamma(block, n)
+    G = AG - mttkrp(Z, block, n)
     g2 = float(np.sum(G * G))
-    if g2 == 0.0 or a2 / g2 > W_CAP:
+    ag2 = float(np.sum(AG * AG))
+    if g2 <= (G_ZERO_REL ** 2) * ag2 or a2 / g2 > W_CAP:
         return W_CAP
     return a2 / g2
 

@@ -354,7 +354,8 @@ __device__ double block_sum(double v, double* sh) {
   return s;
 }
 
-__global__ void k_grad_sq(FactorPtrArgs f, int n, const double* __restrict__ M, double* out, int slot) {
+__global__ void k_grad_sq(FactorPtrArgs f, int n, const double* __restrict__ M, double* out, int slot,
+                          int slot_ag) {
   __shared__ double G[kR * kR];
   __shared__ double sh[32];
   const int R = f.R;
@@ -362,7 +363,7 @@ __global__ void k_grad_sq(FactorPtrArgs f, int n, const double* __restrict__ M, 
   __syncthreads();
   const int64_t I = f.I[n];
   const double* A = f.A[n];
-  double acc = 0.0;
+  double acc = 0.0, acc_ag = 0.0;
   for (int64_t e = threadIdx.x; e < I * R; e += blockDim.x) {
     const int64_t i = e % I;
     const int r = (int)(e / I);
@@ -370,13 +371,20 @@ __global__ void k_grad_sq(FactorPtrArgs f, int n, const double* __restrict__ M, 
     for (int k = 0; k < R; ++k) s += A[i + I * k] * G[k * R + r];
     const double g = s - M[e];
     acc += g * g;
+    acc_ag += s * s;
   }
   const double tot = block_sum(acc, sh);
-  if (threadIdx.x == 0) out[slot] = tot;
+  __syncthreads();
+  const double tot_ag = block_sum(acc_ag, sh);
+  if (threadIdx.x == 0) {
+    out[slot] = tot;
+    if (slot_ag >= 0) out[slot_ag] = tot_ag;
+  }
 }
 
-int launch_grad_sq(const FactorSet& f, int mode, const double* M, double* out, int slot, cudaStream_t st) {
-  k_grad_sq<<<1, 512, 0, st>>>(fargs(f), mode, M, out, slot);
+int launch_grad_sq(const FactorSet& f, int mode, const double* M, double* out, int slot, cudaStream_t st,
+                   int slot_ag) {
+  k_grad_sq<<<1, 512, 0, st>>>(fargs(f), mode, M, out, slot, slot_ag);
   CPMG_CUDA_TRY(cudaGetLastError());
   return CPMG_OK;
 }
@@ -626,18 +634,20 @@ int launch_transform(int64_t I, const double* Pw, double* Rhat, double* work, cu
   return CPMG_OK;
 }
 
-__global__ void k_block_weights(int nblk, const double* a2, const double* g2, double* w) {
+__global__ void k_block_weights(int nblk, const double* a2, const double* g2, const double* ag2, double tau2,
+                                double* w) {
   const int k = threadIdx.x;
   if (k < nblk) {
     const double g = g2[k];
-    double v = (g == 0.0) ? 1e30 : a2[k] / g;
+    double v = (g <= tau2 * ag2[k]) ? 1e30 : a2[k] / g;
     if (!(v <= 1e30)) v = 1e30;
     w[k] = v;
   }
 }
 
-int launch_block_weights(int nblk, const double* a2, const double* g2, double* w, cudaStream_t st) {
-  k_block_weights<<<1, 32, 0, st>>>(nblk, a2, g2, w);
+int launch_block_weights(int nblk, const double* a2, const double* g2, const double* ag2, double tau,
+                         double* w, cudaStream_t st) {
+  k_block_weights<<<1, 32, 0, st>>>(nblk, a2, g2, ag2, tau * tau, w);
   CPMG_CUDA_TRY(cudaGetLastError());
   return CPMG_OK;
 }

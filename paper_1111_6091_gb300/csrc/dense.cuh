@@ -54,9 +54,10 @@ int launch_sort(const FactorSet& f, double* scratch_R2, cudaStream_t st);
 // H = A^(n) Gamma^(n) - M  (Eq. FASop, = G^(n) of Eq. gradEqn); out may alias nothing.
 int launch_fas_op(const FactorSet& f, int mode, const double* M, double* H, cudaStream_t st);
 
-// sum_{i,r} (A^(n) Gamma^(n) - M)^2 into out[slot] (float64; deterministic).
+// sum_{i,r} (A^(n) Gamma^(n) - M)^2 into out[slot] (float64; deterministic) and, when
+// slot_ag >= 0, sum (A^(n) Gamma^(n))^2 into out[slot_ag].
 int launch_grad_sq(const FactorSet& f, int mode, const double* M, double* out, int slot,
-                   cudaStream_t st);
+                   cudaStream_t st, int slot_ag = -1);
 
 // Squared Frobenius norm of a device matrix into out[slot].
 int launch_sq_norm(const double* X, int64_t n, double* out, int slot, cudaStream_t st);
@@ -86,8 +87,10 @@ int launch_interp(int64_t I, int R, int nblk, const double* const* Uptr, const d
 // B = P^T P = L L^T (tridiagonal, so L is bidiagonal).  Section 4.1.
 int launch_transform(int64_t I, const double* Pw, double* Rhat, double* work, cudaStream_t st);
 
-// LS block weights (Eq. interpweights): w[k] = a2[k] / g2[k], capped at 1e30.
-int launch_block_weights(int nblk, const double* a2, const double* g2, double* w, cudaStream_t st);
+// LS block weights (Eq. interpweights): w[k] = a2[k] / g2[k], capped at 1e30; a gradient with
+// g2 <= tau^2 ag2 (rounding level of the arithmetic that produced it) counts as zero (the cap).
+int launch_block_weights(int nblk, const double* a2, const double* g2, const double* ag2, double tau,
+                         double* w, cudaStream_t st);
 
 // Copy / convert helpers.
 int launch_copy_d(double* dst, const double* src, int64_t n, cudaStream_t st);

@@ -290,7 +290,7 @@ static int level_alloc(cpmg_ctx* c, Level& L, int R, int nt) {
   }
   CPMG_TRY(dalloc_t(c, &L.M, (size_t)imax * R));
   CPMG_TRY(dalloc_t(c, &L.twork, 2 * (size_t)icmax + 8));
-  CPMG_TRY(dalloc_t(c, &L.blk, 3 * (size_t)(CPMG_MAX_TEST_BLOCKS + 1) + 8));
+  CPMG_TRY(dalloc_t(c, &L.blk, 40));  // a2 @0, g2 @8, weights @16, |A Gamma|^2 @24
   for (int n = 0; n < N; ++n)
     if (L.co[n]) {
       CPMG_TRY(dalloc_t(c, &L.Rhat[n], (size_t)L.cd[n] * L.s.dims[n]));
@@ -397,13 +397,15 @@ struct Solver {
   double* sortbuf = nullptr;
   int ttm_tc = 0;
 
-  int prec_for(int lvl, int dtype) const {
+  int prec_for(int /*lvl*/, int dtype) const {
     const int hi = dtype == CPMG_F32 ? P_DF : P_FP64;
     switch (policy) {
       case CPMG_PREC_FP32: return P_FP32;
       case CPMG_PREC_FP64: return P_FP64;
       case CPMG_PREC_DF: return hi;
-      default: return (lvl == 0 && refined) ? hi : P_FP32;
+      // Once refined, every level is: FP32 rounding on a coarse level would otherwise enter
+      // each FAS correction at ~1e-7 relative, independent of the fine residual.
+      default: return refined ? hi : P_FP32;
     }
   }
   int gprec(int dtype) const {
@@ -533,10 +535,12 @@ static int build_operators(Solver& S, cpmg_hier* h, int lvl, bool first) {
       U[k] = blocks[k]->A[n];
       CPMG_TRY(launch_sq_norm(blocks[k]->A[n], L.s.dims[n] * R, L.blk, k, S.st));
       CPMG_TRY(run_mttkrp(S.c, L.s, L.Z, L.dtype, *blocks[k], n, prec, L.M));
-      CPMG_TRY(launch_grad_sq(*blocks[k], n, L.M, L.blk, 8 + k, S.st));
+      CPMG_TRY(launch_grad_sq(*blocks[k], n, L.M, L.blk, 8 + k, S.st, 24 + k));
       S.c->launches += 2;
     }
-    CPMG_TRY(launch_block_weights(nb, L.blk, L.blk + 8, L.blk + 16, S.st));
+    // a gradient at the rounding level of the MTTKRP that produced it counts as zero
+    const double tau = prec == P_FP32 ? 1e-5 : 1e-12;
+    CPMG_TRY(launch_block_weights(nb, L.blk, L.blk + 8, L.blk + 24, tau, L.blk + 16, S.st));
     CPMG_TRY(launch_interp(L.s.dims[n], R, nb, U, L.blk + 16, L.Pw[n], S.st));
     CPMG_TRY(launch_transform(L.s.dims[n], L.Pw[n], L.Rhat[n], L.twork, S.st));
     S.c->launches += 3;

@@ -213,3 +213,19 @@ def test_solve_stagnation_rebuild_once(monkeypatch):
     r = MG.mg_fas_solve(p.Z, s.levels, p.A0, s.tfms, o)
     assert r.restarted and len(calls) == 1
     assert r.solve_cycles == 10
+
+
+def test_last_mode_gradient_is_zero_after_als_so_weights_cap():
+    """After one ALS iteration the last mode's gradient vanishes (exact least-squares update,
+    then a column rescaling that keeps it zero), so its block weights hit the cap and the
+    interpolation of that mode is the unweighted fit, whatever the rounding noise."""
+    p = synth.make_problem((12, 10, 8), 3, congruence=0.5, eta_homo=0.1, dtype=np.float64, seed=7)
+    blocks = [ALS.als_sweep(p.Z, b) for b in p.tfms]
+    for b in blocks:
+        G = T.gradient(p.Z, b, 2)
+        assert np.linalg.norm(G) <= 1e-12 * np.linalg.norm(b[2] @ T.gamma(b, 2))
+        assert MG.block_weight(p.Z, b, 2) == MG.W_CAP
+        assert MG.block_weight(p.Z, b, 0) < MG.W_CAP
+    U = np.hstack([b[2] for b in blocks])
+    w = np.array([MG.block_weight(p.Z, b, 2) for b in blocks]).repeat(3)
+    assert np.allclose(MG.interpolation(U, w, 8), MG.interpolation(U, np.ones(6), 8), rtol=1e-12)
