@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Benchmark: time-to-tolerance of the multilevel CP solver on one GPU.
+
+Workload (one step): the 100x100x100 float32 tensor of rank 5 whose factor columns have
+pairwise congruence 0.9, with 1% homoscedastic and 5% heteroscedastic noise (seeded
+synthetic data), decomposed by the "Multilevel" solver (CP-AMG-mult setup cycles, then
+CP-FAS solve cycles with the one-time rebuild, then plain ALS if stagnation persists)
+from a fixed N(0,1) start until g < 1e-8 (Eq. gradConv), levels 100/50/25/13, MIXED
+precision (FP32 sweeps, float64-accurate sweeps near the FP32 floor).
+
+Timing: W untimed steps, then K steps each bracketed by CUDA events on the library's
+stream, with a 512 MB write between steps to flush the 126 MB L2 (the tensor is 4 MB).
+The finest-level MTTKRP launches inside the timed steps are timed with events by the
+library (roofline).  The end-to-end number repeats the solve through the same C ABI call
+with pinned host buffers, the copies inside the timed region.  A second measurement
+times the FP32 MTTKRP of the 400x400x400 rank-10 tensor (256 MB, larger than L2) against
+the measured HBM peak.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS, RANK, CONG, ETA1, ETA2, SEED = (100, 100, 100), 5, 0.9, 0.01, 0.05, 0
+COARSEST = (13, 13, 13)
+TOL = 1e-8
+METRIC = "time-to-tol (rel err 1e-8)"
+WORKLOAD = "dense 100x100x100 fp32, R=5, congruence 0.9, noise 1%+5%, multilevel 4 levels, g<1e-8"
+
+
+def problem():
+    from paper_1111_6091_gb300 import synth
+    return synth.make_problem(DIMS, RANK, congruence=CONG, eta_homo=ETA1, eta_hetero=ETA2,
+                              dtype=np.float32, seed=SEED)
+
+
+def config(extra=None):
+    c = {"workload": WORKLOAD, "dims": list(DIMS), "rank": RANK, "congruence": CONG,
+         "noise": [ETA1, ETA2], "tol": TOL, "solver": "multilevel (setup + FAS + ALS fallback)",
+         "precision": "mixed fp32 / float-pair", "l2": "flushed between steps (512 MB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+def oracle_solve(p):
+    from oracle import multigrid as MG
+    o = MG.Options(coarsest=COARSEST, tol=TOL, als_fallback=True)
+    t = time.perf_counter()
+    r = MG.multilevel(p.Z.astype(np.float64), p.A0, p.tfms, o)
+    return time.perf_counter() - t, r
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        return max(n) if n else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = problem()
+    for _ in range(min(args.warmup, 1)):
+        oracle_solve(p)
+    times = []
+    r = None
+    for _ in range(args.steps):
+        dt, r = oracle_solve(p)
+        times.append(dt)
+    v = statistics.mean(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * v,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config(),
+        "cpu_baseline": {"value": v, "unit": "s", "cores": blas_threads(), "kind": "oracle",
+                         "sample": "full solve of the workload by the FP64 NumPy oracle"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_cycles": {"setup": r.setup_cycles, "solve": r.solve_cycles,
+                          "als": getattr(r, "als_iters", 0), "converged": bool(r.converged)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU
+class Clocks:
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_gpu(args):
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    ctx = cpmg.Context(local, stream=stream.cuda_stream)
+    p = problem()
+    opts = cpmg.make_opts(precision=cpmg.PREC_MIXED, tol=TOL, coarsest=COARSEST, als_fallback=1)
+
+    with torch.cuda.stream(stream):
+        Z = cpmg.colmajor(p.Z)
+        A0 = [cpmg.colmajor(a) for a in p.A0]
+        T0 = [[cpmg.colmajor(a) for a in b] for b in p.tfms]
+        A = [a.clone() for a in A0]
+        T = [[a.clone() for a in b] for b in T0]
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def reset():
+        for a, a0 in zip(A, A0):
+            a.copy_(a0)
+        for b, b0 in zip(T, T0):
+            for a, a0 in zip(b, b0):
+                a.copy_(a0)
+
+    def step():
+        return cpmg.cpmg_decompose(ctx, Z, A, T, opts)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            reset()
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = Clocks()
+        clocks.start()
+        ctx.profile(True)
+        ctx.profile_reset()
+        launches0 = ctx.launches()
+        ms, results = [], []
+        for _ in range(args.steps):
+            reset()
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            results.append(step())
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        prof = [ctx.profile_read(k) for k in range(3)]
+        ctx.profile(False)
+        launches = ctx.launches() - launches0
+        clk = clocks.stop()
+    t_step = max(ms_i for ms_i in [statistics.mean(ms)])
+    if world > 1:
+        t = torch.tensor([t_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+
+    # end to end through the C ABI with pinned host buffers
+    Zh = cpmg.colmajor(p.Z, device="cpu", pin=True)
+    Ah = [cpmg.colmajor(a, device="cpu", pin=True) for a in p.A0]
+    Th = [[cpmg.colmajor(a, device="cpu", pin=True) for a in b] for b in p.tfms]
+    e2e = []
+    for _ in range(args.steps):
+        for a, a0 in zip(Ah, p.A0):
+            a.copy_(torch.from_numpy(np.ascontiguousarray(a0.T)))
+        for b, b0 in zip(Th, p.tfms):
+            for a, a0 in zip(b, b0):
+                a.copy_(torch.from_numpy(np.ascontiguousarray(a0.T)))
+        with torch.cuda.stream(stream):
+            flush.fill_(2.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cpmg.cpmg_decompose(ctx, Zh, Ah, Th, opts)
+            torch.cuda.synchronize()
+            e2e.append(time.perf_counter() - t0)
+    h2d = Zh.numel() * 4 + sum(a.numel() * 8 for a in Ah) + sum(a.numel() * 8 for b in Th for a in b)
+    d2h = sum(a.numel() * 8 for a in Ah) + sum(a.numel() * 8 for b in Th for a in b)
+
+    # dominant kernel of the timed steps: the finest-level MTTKRP main kernel
+    kinds = ["fp32", "float-pair", "fp64"]
+    tot = [x[0] for x in prof]
+    k = int(np.argmax(tot))
+    ms_k, n_k, bytes_k = prof[k]
+    hbm, how = peaks()
+    avg_s = ms_k * 1e-3 / max(n_k, 1)
+    achieved = bytes_k / avg_s / 1e9 if n_k else None
+
+    # 400^3 rank-10 FP32 MTTKRP bandwidth (inputs larger than L2)
+    from paper_1111_6091_gb300 import synth
+    p4 = synth.make_problem((400, 400, 400), 10, congruence=0.95, eta_homo=0.01, dtype=np.float32, seed=0)
+    with torch.cuda.stream(stream):
+        Z4 = cpmg.colmajor(p4.Z)
+        A4 = [cpmg.colmajor(a) for a in p4.A0]
+        o4 = cpmg.make_opts(precision=cpmg.PREC_FP32, check_every=0)
+        cpmg.cp_als_sweep(ctx, Z4, A4, 3, o4)
+        ctx.profile(True)
+        ctx.profile_reset()
+        cpmg.cp_als_sweep(ctx, Z4, A4, 10, o4)
+        ms4, n4, b4 = ctx.profile_read(0)
+        ctx.profile(False)
+    gbs4 = b4 / (ms4 * 1e-3 / n4) / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, r = oracle_solve(p)
+        cpu = {"value": dt, "unit": "s", "cores": blas_threads(), "kind": "oracle",
+               "sample": "one full solve of the workload by the FP64 NumPy oracle (same solver and start)",
+               "oracle_cycles": {"setup": r.setup_cycles, "solve": r.solve_cycles,
+                                 "als": getattr(r, "als_iters", 0)}}
+
+    res = results[-1]
+    line = {
+        "metric": METRIC, "value": t_step * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": False,
+        "scaling": "weak" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": {"bound": "hbm", "kernel": f"mttkrp_main ({kinds[k]}, 100^3 finest level)",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm if achieved else None, "traffic": None,
+                     "launches": n_k, "avg_us": avg_s * 1e6, "peak_source": how,
+                     "note": "4 MB tensor is L2-resident inside a solve; frac is against HBM"},
+        "mttkrp_400cubed_fp32": {"achieved": gbs4, "peak": hbm, "unit": "GB/s", "frac": gbs4 / hbm,
+                                 "avg_us": ms4 * 1e3 / n4, "launches": n4, "peak_source": how},
+        "cpu_baseline": cpu,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "solver": {k2: res[k2] for k2 in ("g", "f", "iters_setup", "iters_solve", "iters_als", "restarted",
+                                          "refine_sweeps", "levels", "status")},
+        "step_ms": ms,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_mttkrp_case(args):
+    """Small case for profiler captures: two FP32 ALS sweeps on the 400^3 rank-10 tensor
+    (six MTTKRP main-kernel launches)."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg, synth
+    p4 = synth.make_problem((400, 400, 400), 10, congruence=0.95, eta_homo=0.01, dtype=np.float32, seed=0)
+    ctx = cpmg.Context(0)
+    Z4 = cpmg.colmajor(p4.Z)
+    A4 = [cpmg.colmajor(a) for a in p4.A0]
+    prec = {"fp32": cpmg.PREC_FP32, "df": cpmg.PREC_DF, "fp64": cpmg.PREC_FP64}[args.case_prec]
+    r = cpmg.cp_als_sweep(ctx, Z4, A4, 2, precision=prec, check_every=0)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "mttkrp 400^3 R=10", "precision": args.case_prec, "f": r["f"]}))
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--mttkrp-case", action="store_true", help="profiler case: 2 sweeps at 400^3")
+    ap.add_argument("--case-prec", default="fp32", choices=["fp32", "df", "fp64"])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl != "reference":
+        from paper_1111_6091_gb300 import build
+        build.build()
+    if args.mttkrp_case:
+        run_mttkrp_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -393,6 +393,8 @@ struct Solver {
   int policy;
   bool refined = false;
   int refine_sweeps = 0;
+  double g_best = -1.0;
+  int stall = 0;
   double znorm = 0.0;
   double* sortbuf = nullptr;
   int ttm_tc = 0;
@@ -479,12 +481,20 @@ static int eval_g(Solver& S, const Level& L, FactorSet& f, double* g, double* mn
   return CPMG_OK;
 }
 
-// MIXED policy: switch the finest level to float64-accurate sweeps near the FP32 floor.
-static void maybe_switch(Solver& S, double g, double mnorm, double g_prev) {
+// MIXED policy: switch to float64-accurate sweeps once g is within a factor K of the
+// FP32 floor, estimated as eps_32 ||M|| / ||Z|| (the size of one FP32 rounding of the
+// MTTKRP seen through Eq. gradConv), or after 20 checks without a new smallest g.
+static void maybe_switch(Solver& S, double g, double mnorm, double /*g_prev*/) {
   if (S.policy != CPMG_PREC_MIXED || S.refined) return;
   const double K = S.o.mixed_switch > 0 ? S.o.mixed_switch : 64.0;
   const double floor_est = K * 5.960464477539063e-08 * mnorm / S.znorm;
-  if (g < floor_est || (g_prev > 0 && g >= g_prev)) S.refined = true;
+  if (S.g_best < 0 || g < S.g_best) {
+    S.g_best = g;
+    S.stall = 0;
+  } else {
+    ++S.stall;
+  }
+  if (g < floor_est || S.stall >= 20) S.refined = true;
 }
 
 static int tensor_norm(Solver& S, const Level& L, FactorSet& f, double* znorm) {
