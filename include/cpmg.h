@@ -149,6 +149,26 @@ int cpmg_mttkrp(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, const double* const*
 int cpmg_ttm(cpmg_ctx* ctx, const cpmg_tensor* Z, const double* const* Rhat, const int64_t* Ic,
              int tensor_cores, void* Y);
 
+/* Allocation-free MTTKRP (the paper has no counterpart: this exists for callers).
+ * Same result and arguments as cpmg_mttkrp, without a context, for callers that cannot
+ * allocate device memory (their own allocator already owns the GPU, or they cannot afford
+ * the synchronization cudaMalloc/cudaFree may cause).  The kernels' scratch is a fixed
+ * array of CPMG_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until the
+ * process exits; the call itself allocates nothing.
+ *  - Z, A, M: device pointers on the current device (Z->mem must be CPMG_MEM_DEVICE).
+ *  - cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default stream).  The call
+ *    only enqueues work: M is ready when the stream reaches that point.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the array: calls whose work overlaps on the GPU (unordered streams)
+ *    race and corrupt each other.  Calls ordered on one stream are safe.
+ *  - Returns CPMG_OUT_OF_BUDGET when the problem's scratch (per-CTA partial sums and
+ *    Khatri-Rao tables, even with the fewest work units) exceeds the array,
+ *    CPMG_INVALID_ARG for bad shapes or pointers, CPMG_CUDA_ERROR on a failed CUDA call. */
+#define CPMG_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+int cpmg_mttkrp_noalloc(const cpmg_tensor* Z, int R, const double* const* A, int mode, int precision,
+                        double* M, void* cuda_stream);
+
 /* f = 1/2 ||Z - [[A]]||^2 (Eq. CPfunctional, element by element in float64) and
  * g (Eq. gradConv, with float64-accurate MTTKRPs).  Either output may be NULL. */
 int cpmg_eval_fg(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, const double* const* A,
