@@ -226,7 +226,7 @@ static int run_mttkrp(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, con
   }
   const double* Aptrs[kMaxModes];
   for (int m = 0; m < kMaxModes; ++m) Aptrs[m] = f.A[m];
-  CPMG_TRY(mttkrp_run(*p, s, Z, Aptrs, w, M, c->stream, e0, e1));
+  CPMG_TRY(mttkrp_run(*p, s, Z, Aptrs, w, M, c->stream, e0, e1, c->dstatus + 1));
   c->launches += (p->has_in || p->has_out) ? 3 : 2;
   if (c->pending.size() > 512) CPMG_TRY(profile_collect(c));
   return CPMG_OK;
@@ -469,7 +469,9 @@ static int eval_g(Solver& S, const Level& L, FactorSet& f, double* g, double* mn
     S.c->launches += 2;
   }
   CPMG_CUDA_TRY(cudaMemcpyAsync(S.c->hsc, S.c->dsc, 128 * sizeof(double), cudaMemcpyDeviceToHost, S.st));
+  CPMG_CUDA_TRY(cudaMemcpyAsync(S.c->hsc + 128, S.c->dstatus, 4 * sizeof(int), cudaMemcpyDeviceToHost, S.st));
   CPMG_CUDA_TRY(cudaStreamSynchronize(S.st));
+  if (reinterpret_cast<const int*>(S.c->hsc + 128)[1] != 0) return CPMG_TIMEOUT;
   double sg = 0.0, sm = 0.0;
   for (int n = 0; n < f.N; ++n) {
     sg += S.c->hsc[n];
@@ -502,8 +504,10 @@ static int tensor_norm(Solver& S, const Level& L, FactorSet& f, double* znorm) {
   CPMG_TRY(dalloc_t(S.c, &partial, 2 * 1024 + 8));
   int st = launch_f_direct(L.s, L.Z, L.dtype, f, partial, S.c->dsc + 200, S.st);
   if (st == CPMG_OK) {
-    cudaMemcpyAsync(S.c->hsc + 200, S.c->dsc + 200, 2 * sizeof(double), cudaMemcpyDeviceToHost, S.st);
-    if (cudaStreamSynchronize(S.st) != cudaSuccess) st = CPMG_CUDA_ERROR;
+    if (cudaMemcpyAsync(S.c->hsc + 200, S.c->dsc + 200, 2 * sizeof(double), cudaMemcpyDeviceToHost, S.st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(S.st) != cudaSuccess)
+      st = CPMG_CUDA_ERROR;
   }
   dfree(S.c, partial);
   S.c->launches += 2;
@@ -516,8 +520,10 @@ static int eval_f(Solver& S, const Level& L, FactorSet& f, double* fval, double*
   CPMG_TRY(dalloc_t(S.c, &partial, 2 * 1024 + 8));
   int st = launch_f_direct(L.s, L.Z, L.dtype, f, partial, S.c->dsc + 200, S.st);
   if (st == CPMG_OK) {
-    cudaMemcpyAsync(S.c->hsc + 200, S.c->dsc + 200, 2 * sizeof(double), cudaMemcpyDeviceToHost, S.st);
-    if (cudaStreamSynchronize(S.st) != cudaSuccess) st = CPMG_CUDA_ERROR;
+    if (cudaMemcpyAsync(S.c->hsc + 200, S.c->dsc + 200, 2 * sizeof(double), cudaMemcpyDeviceToHost, S.st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(S.st) != cudaSuccess)
+      st = CPMG_CUDA_ERROR;
   }
   dfree(S.c, partial);
   S.c->launches += 2;
@@ -842,6 +848,7 @@ int cpmg_profile_reset(cpmg_ctx* c) {
 
 int cpmg_mttkrp(cpmg_ctx* c, const cpmg_tensor* Z, int R, const double* const* A, int mode, int precision,
                 double* M) {
+  cudaGetLastError();  // an error left pending by the caller is not this call's
   if (!c || !A || !M) return CPMG_INVALID_ARG;
   CPMG_TRY(check_tensor(Z));
   if (Z->mem != CPMG_MEM_DEVICE) return CPMG_INVALID_ARG;
@@ -869,6 +876,7 @@ int cpmg_mttkrp(cpmg_ctx* c, const cpmg_tensor* Z, int R, const double* const* A
 
 int cpmg_ttm(cpmg_ctx* c, const cpmg_tensor* Z, const double* const* Rhat, const int64_t* Ic, int tensor_cores,
              void* Y) {
+  cudaGetLastError();  // an error left pending by the caller is not this call's
   if (!c || !Rhat || !Ic || !Y) return CPMG_INVALID_ARG;
   CPMG_TRY(check_tensor(Z));
   if (Z->mem != CPMG_MEM_DEVICE) return CPMG_INVALID_ARG;
@@ -892,6 +900,7 @@ int cpmg_ttm(cpmg_ctx* c, const cpmg_tensor* Z, const double* const* Rhat, const
 }
 
 int cpmg_eval_fg(cpmg_ctx* c, const cpmg_tensor* Z, int R, const double* const* A, double* f, double* g) {
+  cudaGetLastError();  // an error left pending by the caller is not this call's
   if (!c || !A) return CPMG_INVALID_ARG;
   CPMG_TRY(check_tensor(Z));
   if (Z->mem != CPMG_MEM_DEVICE || R < 1 || R > CPMG_MAX_RANK) return CPMG_INVALID_ARG;
@@ -925,6 +934,7 @@ int cpmg_eval_fg(cpmg_ctx* c, const cpmg_tensor* Z, int R, const double* const* 
 
 int cp_als_sweep(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A, int nsweeps, const cpmg_opts* opts,
                  cpmg_result* res) {
+  cudaGetLastError();  // an error left pending by the caller is not this call's
   const double t0 = now_s();
   if (!c || !A || nsweeps < 0) return CPMG_INVALID_ARG;
   CPMG_TRY(check_tensor(Z));
@@ -1004,6 +1014,7 @@ static int setup_cycles(Solver& S, cpmg_hier* h, int* cycles, std::vector<double
 
 int mg_setup(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A_boot, double* const* A_test,
              const cpmg_opts* opts, cpmg_hier** out, cpmg_result* res) {
+  cudaGetLastError();  // an error left pending by the caller is not this call's
   const double t0 = now_s();
   if (!c || !A_boot || !out) return CPMG_INVALID_ARG;
   *out = nullptr;
@@ -1102,6 +1113,7 @@ static int solve_cycles(Solver& S, cpmg_hier* h, int cycles_done, int* solve, in
 
 int mg_fas_solve(cpmg_ctx* c, cpmg_hier* h, const cpmg_tensor* Z, double* const* A, const cpmg_opts* opts,
                  cpmg_result* res) {
+  cudaGetLastError();  // an error left pending by the caller is not this call's
   const double t0 = now_s();
   if (!c || !h || !A) return CPMG_INVALID_ARG;
   CPMG_TRY(check_tensor(Z));
@@ -1172,6 +1184,7 @@ int cpmg_hier_level_info(const cpmg_hier* h, int level, int64_t* dims, int* coar
 
 int cpmg_decompose(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A, double* const* A_test,
                    const cpmg_opts* opts, cpmg_result* res) {
+  cudaGetLastError();  // an error left pending by the caller is not this call's
   const double t0 = now_s();
   if (!c || !A) return CPMG_INVALID_ARG;
   CPMG_TRY(check_tensor(Z));

@@ -24,14 +24,26 @@ struct MttkrpPlan {
   bool has_in = false, has_out = false;
   int in_modes[kMaxModes], n_in = 0;     // modes whose KR product forms Kin
   int out_modes[kMaxModes], n_out = 0;   // modes whose KR product forms Kout
+  // shared-memory staging by bulk copies (TMA): eligibility and ring geometry
+  bool use_tma = false;
+  int CPS = 1, S = 2;          // columns per group per stage, stages
+  int64_t ROWS = 0;            // rows per column held in a stage
+  bool contiguous = false;     // a stage is one contiguous byte range
+  uint32_t stage_stride = 0, w_off = 0, w_stride = 0, bar_off = 0, col_off = 0, stage_off = 0, red_off = 0;
+  size_t smem_tma = 0;
+  bool tab_smem = false;       // Khatri-Rao tables staged into shared memory
+  uint32_t tab_off = 0;
+  int nw = 1;                  // per-unit partials (consumer warps of the TMA kernel, mode > 0)
+  int64_t grid = 0;            // CTAs launched (persistent over unit ranges for mode > 0)
   size_t table_bytes = 0;      // bytes of one table element (4, 8 or 8 for float2)
   size_t part_elem = 0;        // bytes of one partial entry
   size_t partial_bytes() const;
   size_t tables_bytes() const;  // A1 + Kin + Kout
 };
 
+// allow_tma = false forces the register-load kernel (smaller scratch: no full row table).
 int mttkrp_plan(const Shape& s, int mode, int R, int prec, int zdtype, const void* Z, int num_sms,
-                MttkrpPlan* p);
+                MttkrpPlan* p, bool allow_tma = true);
 
 // Device buffers the MTTKRP needs besides Z and the factors.
 struct MttkrpScratch {
@@ -43,6 +55,6 @@ struct MttkrpScratch {
 // kernel and the ordered reduction into M (float64, I_n x R column-major).
 int mttkrp_run(const MttkrpPlan& p, const Shape& s, const void* Z, const double* const* A_dev_ptrs,
                const MttkrpScratch& w, double* M, cudaStream_t st, cudaEvent_t ev0 = nullptr,
-               cudaEvent_t ev1 = nullptr);
+               cudaEvent_t ev1 = nullptr, int* err = nullptr);
 
 }  // namespace cpmg

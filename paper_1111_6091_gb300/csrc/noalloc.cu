@@ -13,6 +13,7 @@
 // whose work overlaps on the GPU (different streams, no ordering between them) race on
 // it and corrupt each other's results.  Calls ordered on one stream are safe.  Nothing
 // in the array needs to start at zero: each call writes every byte it later reads.
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -77,11 +78,18 @@ extern "C" int cpmg_mttkrp_noalloc(const cpmg_tensor* Z, int R, const double* co
   CPMG_TRY(scratch_address(device, &base));
 
   MttkrpPlan p;
-  CPMG_TRY(mttkrp_plan(s, mode, R, prec, Z->dtype, Z->data, sms, &p));
-  // Fewer, larger work units until the partial sums and the tables fit the fixed scratch.
-  while (p.partial_bytes() + p.tables_bytes() > kScratchBytes && p.C > 1) {
-    p.C = (p.C + 1) / 2;
-    p.nunits = p.In * p.nseg * p.C;
+  // The bulk-copy kernel needs a full Khatri-Rao row table; when that does not fit, the
+  // register-load kernel (two small tables) serves instead.
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    CPMG_TRY(mttkrp_plan(s, mode, R, prec, Z->dtype, Z->data, sms, &p, attempt == 0));
+    // Fewer, larger work units until the partial sums and the tables fit the fixed scratch.
+    while (p.partial_bytes() + p.tables_bytes() > kScratchBytes && p.C > 1) {
+      p.C = (p.C + 1) / 2;
+      p.nunits = p.In * p.nseg * p.C;
+      // one unit per CTA, except the persistent kernel that spreads unit ranges over its CTAs
+      p.grid = (p.use_tma && p.mode != 0) ? std::min<int64_t>(p.grid, p.nunits) : p.nunits;
+    }
+    if (p.partial_bytes() + p.tables_bytes() + 256 <= kScratchBytes) break;
   }
   const size_t tables = p.tables_bytes();
   if (p.partial_bytes() + tables > kScratchBytes) return CPMG_OUT_OF_BUDGET;
