@@ -102,7 +102,10 @@ typedef struct {
                                      /*    (an addition; the paper stops after one rebuild)   */
   double mixed_switch;               /* MIXED: switch to float64-accurate sweeps when
                                         g < mixed_switch * (FP32 floor estimate); <= 0: 64     */
-  int check_every;                   /* cp_als_sweep: evaluate g every k sweeps (0 = never)   */
+  int check_every;                   /* cp_als_sweep: exact g every k sweeps (0 = never; < 0 =
+                                        adaptive interval, at most 32, from the observed rate)  */
+  int use_graphs;                    /* 1: capture sweeps / cycles as CUDA graphs and replay
+                                        (needs a context stream other than the legacy default) */
 } cpmg_opts;
 
 typedef struct {
@@ -180,7 +183,7 @@ int cpmg_eval_fg(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, const double* const
  * n = 1..N, each A^(n) <- Z_(n) Phi^(n) (Gamma^(n))^+ with Gamma^(n) the Hadamard product
  * of the other modes' Grams (Eq. Gamma), followed by the normalization of Eq. ALSnorm;
  * the components are sorted by decreasing lambda at the end (end of Section 3).
- * If opts->check_every > 0 the call stops once g < opts->tol.
+ * If opts->check_every != 0 the call stops at the first exact check with g < opts->tol.
  * A[0..N-1]: factor arrays, read as the start and overwritten with the result. */
 int cp_als_sweep(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A, int nsweeps,
                  const cpmg_opts* opts, cpmg_result* result);

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "dense.cuh"
+#include "fused.cuh"
 #include "mttkrp.cuh"
 #include "ttm.cuh"
 
@@ -24,7 +25,8 @@ using namespace cpmg;
 struct ProfEvents {
   cudaEvent_t a, b;
   double bytes;
-  int kind;  // 0: FP32, 1: pairs of floats, 2: FP64 finest-level MTTKRP main kernel
+  int kind;     // 0: FP32, 1: pairs of floats, 2: FP64 finest-level MTTKRP main kernel
+  bool owned;   // recorded inside a CUDA graph: the graph keeps the events
 };
 
 struct cpmg_ctx {
@@ -42,6 +44,7 @@ struct cpmg_ctx {
   std::map<std::string, MttkrpPlan> plans;
   // scalars
   double* dsc = nullptr;   // device scalars (4096)
+  double* gscratch = nullptr;  // block Grams of the fused finish/update kernel
   double* hsc = nullptr;   // pinned host mirror
   int* dstatus = nullptr;
   // profiling of the finest-level MTTKRP main kernel
@@ -53,6 +56,7 @@ struct cpmg_ctx {
   double prof_bytes[3] = {0, 0, 0};
   int64_t launches = 0;
   const void* prof_Z = nullptr;  // tensor whose MTTKRPs are profiled (the finest level)
+  bool capturing = false;        // a CUDA graph capture is open on `stream`
 };
 
 namespace cpmg {
@@ -184,7 +188,7 @@ static double algorithmic_bytes(const Shape& s, int mode, int R, int dtype) {
 }
 
 static int profile_collect(cpmg_ctx* c) {
-  if (c->pending.empty()) return CPMG_OK;
+  if (c->pending.empty() || c->capturing) return CPMG_OK;
   CPMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
   for (auto& p : c->pending) {
     float ms = 0.f;
@@ -193,15 +197,53 @@ static int profile_collect(cpmg_ctx* c) {
       c->prof_launches[p.kind] += 1;
       c->prof_bytes[p.kind] += p.bytes;
     }
-    c->pool.push_back(p);
+    if (!p.owned) c->pool.push_back(p);
   }
   c->pending.clear();
   cudaGetLastError();
   return CPMG_OK;
 }
 
+// ============================================================================ CUDA graphs
+// A relaxation sweep, a setup cycle or a CP-FAS V-cycle is a fixed sequence of launches (no
+// host decisions inside), so it is captured once and replayed as one graph launch.  Graphs are
+// owned by the object whose buffers they reference (a hierarchy, or one cp_als_sweep call) and
+// are destroyed with it; a graph also records the finest-level tensor pointer it was captured
+// with and is re-captured if that changes.
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  const void* z0 = nullptr;
+  int64_t dlaunch = 0;
+  int drefine = 0;
+  std::vector<ProfEvents> events;
+};
+
+struct GraphCache {
+  std::map<std::string, GraphEntry> m;
+  void clear() {
+    for (auto& kv : m) {
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      for (auto& e : kv.second.events) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+      }
+    }
+    m.clear();
+  }
+};
+
+// kind < 0: M = MTTKRP (reduced by the finish kernel).  kind 0 / 1: the MTTKRP followed by the
+// fused reduction + ALS solve / Gauss-Seidel (with right-hand side F) + Gram refresh of mode n.
+static int run_mttkrp_k(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, const FactorSet& f, int mode,
+                        int prec, double* M, int kind, const double* F, int gs_sweeps);
+
 static int run_mttkrp(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, const FactorSet& f, int mode,
                       int prec, double* M) {
+  return run_mttkrp_k(c, s, Z, dtype, f, mode, prec, M, -1, nullptr, 0);
+}
+
+static int run_mttkrp_k(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, const FactorSet& f, int mode,
+                        int prec, double* M, int kind, const double* F, int gs_sweeps) {
   const MttkrpPlan* p = nullptr;
   CPMG_TRY(get_plan(c, s, mode, f.R, prec, dtype, Z, &p));
   CPMG_TRY(ensure_scratch(c, p->partial_bytes(), p->tables_bytes()));
@@ -211,7 +253,7 @@ static int run_mttkrp(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, con
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profile && Z == c->prof_Z) {
     ProfEvents pe;
-    if (!c->pool.empty()) {
+    if (!c->pool.empty() && !c->capturing) {
       pe = c->pool.back();
       c->pool.pop_back();
     } else {
@@ -219,6 +261,7 @@ static int run_mttkrp(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, con
       CPMG_CUDA_TRY(cudaEventCreate(&pe.b));
     }
     pe.bytes = algorithmic_bytes(s, mode, f.R, dtype);
+    pe.owned = c->capturing;
     pe.kind = p->prec == P_FP32 ? 0 : (p->prec == P_DF ? 1 : 2);
     c->pending.push_back(pe);
     e0 = pe.a;
@@ -226,8 +269,11 @@ static int run_mttkrp(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, con
   }
   const double* Aptrs[kMaxModes];
   for (int m = 0; m < kMaxModes; ++m) Aptrs[m] = f.A[m];
-  CPMG_TRY(mttkrp_run(*p, s, Z, Aptrs, w, M, c->stream, e0, e1, c->dstatus + 1));
-  c->launches += (p->has_in || p->has_out) ? 3 : 2;
+  CPMG_TRY(mttkrp_run(*p, s, Z, Aptrs, w, M, c->stream, e0, e1, c->dstatus + 1, kind < 0, c->capturing));
+  c->launches += (p->use_tma || p->has_in || p->has_out) ? 3 : 2;
+  if (kind >= 0)
+    CPMG_TRY(launch_finish_update(*p, w, f, mode, kind, F, gs_sweeps, nullptr, c->gscratch, c->dstatus + 2,
+                                  c->dstatus, c->stream));
   if (c->pending.size() > 512) CPMG_TRY(profile_collect(c));
   return CPMG_OK;
 }
@@ -266,6 +312,7 @@ struct cpmg_hier {
   double* Aold = nullptr;  // backing of a FactorSet copy for the restart rule
   FactorSet Aprev;
   int ttm_tc = 0;
+  GraphCache graphs;
 };
 
 static int level_alloc(cpmg_ctx* c, Level& L, int R, int nt) {
@@ -318,6 +365,9 @@ static void level_free(cpmg_ctx* c, Level& L) {
 static void hier_destroy(cpmg_hier* h) {
   if (!h) return;
   cpmg_ctx* c = h->c;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  profile_collect(c);  // graph-owned profiling events leave the pending list before they die
+  h->graphs.clear();
   for (auto& L : h->L) level_free(c, L);
   dfree(c, h->tmp0);
   dfree(c, h->tmp1);
@@ -398,6 +448,9 @@ struct Solver {
   double znorm = 0.0;
   double* sortbuf = nullptr;
   int ttm_tc = 0;
+  GraphCache* gc = nullptr;     // graphs of the object being solved (null: no graphs)
+  const void* z0 = nullptr;     // finest-level tensor the graphs reference
+  bool use_graphs = true;
 
   int prec_for(int /*lvl*/, int dtype) const {
     const int hi = dtype == CPMG_F32 ? P_DF : P_FP64;
@@ -419,11 +472,7 @@ struct Solver {
 // One ALS iteration over all modes plus normalization (Section 3, Eq. ALSnorm).
 static int als_sweep(Solver& S, const Level& L, int lvl, FactorSet& f) {
   const int prec = S.prec_for(lvl, L.dtype);
-  for (int n = 0; n < f.N; ++n) {
-    CPMG_TRY(run_mttkrp(S.c, L.s, L.Z, L.dtype, f, n, prec, L.M));
-    CPMG_TRY(launch_als_update(f, n, L.M, S.c->dstatus, S.st));
-    S.c->launches += 2;
-  }
+  for (int n = 0; n < f.N; ++n) CPMG_TRY(run_mttkrp_k(S.c, L.s, L.Z, L.dtype, f, n, prec, nullptr, 0, nullptr, 0));
   if (lvl == 0 && prec != P_FP32) S.refine_sweeps++;
   CPMG_TRY(launch_normalize(f, S.st));
   S.c->launches += 2;
@@ -443,11 +492,9 @@ static int relax_als(Solver& S, const Level& L, int lvl, FactorSet& f, int iters
 static int relax_bngs(Solver& S, const Level& L, int lvl, FactorSet& f, bool hasF, int iters, bool top) {
   const int prec = S.prec_for(lvl, L.dtype);
   for (int it = 0; it < iters; ++it) {
-    for (int n = 0; n < f.N; ++n) {
-      CPMG_TRY(run_mttkrp(S.c, L.s, L.Z, L.dtype, f, n, prec, L.M));
-      CPMG_TRY(launch_gs_update(f, n, L.M, hasF ? L.F[n] : nullptr, S.o.gs_sweeps, S.st));
-      S.c->launches += 2;
-    }
+    for (int n = 0; n < f.N; ++n)
+      CPMG_TRY(run_mttkrp_k(S.c, L.s, L.Z, L.dtype, f, n, prec, nullptr, 1, hasF ? L.F[n] : nullptr,
+                            S.o.gs_sweeps));
     if (lvl == 0 && prec != P_FP32) S.refine_sweeps++;
     if (top) {
       CPMG_TRY(launch_normalize(f, S.st));
@@ -458,9 +505,10 @@ static int relax_bngs(Solver& S, const Level& L, int lvl, FactorSet& f, bool has
   return CPMG_OK;
 }
 
-// g of Eq. gradConv on level L with float64-accurate MTTKRPs; also returns ||M|| for the
-// precision switch.  Synchronizes.
-static int eval_g(Solver& S, const Level& L, FactorSet& f, double* g, double* mnorm) {
+// g of Eq. gradConv on level L with float64-accurate MTTKRPs, in two parts: the launches
+// (capturable: MTTKRPs, gradient norms, copies of the scalars to pinned host memory) and the
+// host read after a synchronization.  Also yields ||M|| for the precision switch.
+static int eval_g_launch(Solver& S, const Level& L, FactorSet& f) {
   const int prec = S.gprec(L.dtype);
   for (int n = 0; n < f.N; ++n) {
     CPMG_TRY(run_mttkrp(S.c, L.s, L.Z, L.dtype, f, n, prec, L.M));
@@ -470,10 +518,14 @@ static int eval_g(Solver& S, const Level& L, FactorSet& f, double* g, double* mn
   }
   CPMG_CUDA_TRY(cudaMemcpyAsync(S.c->hsc, S.c->dsc, 128 * sizeof(double), cudaMemcpyDeviceToHost, S.st));
   CPMG_CUDA_TRY(cudaMemcpyAsync(S.c->hsc + 128, S.c->dstatus, 4 * sizeof(int), cudaMemcpyDeviceToHost, S.st));
+  return CPMG_OK;
+}
+
+static int eval_g_read(Solver& S, int N, double* g, double* mnorm) {
   CPMG_CUDA_TRY(cudaStreamSynchronize(S.st));
   if (reinterpret_cast<const int*>(S.c->hsc + 128)[1] != 0) return CPMG_TIMEOUT;
   double sg = 0.0, sm = 0.0;
-  for (int n = 0; n < f.N; ++n) {
+  for (int n = 0; n < N; ++n) {
     sg += S.c->hsc[n];
     sm += S.c->hsc[64 + n];
   }
@@ -481,6 +533,11 @@ static int eval_g(Solver& S, const Level& L, FactorSet& f, double* g, double* mn
   if (mnorm) *mnorm = std::sqrt(sm);
   if (!std::isfinite(*g)) return CPMG_NUMERIC;
   return CPMG_OK;
+}
+
+static int eval_g(Solver& S, const Level& L, FactorSet& f, double* g, double* mnorm) {
+  CPMG_TRY(eval_g_launch(S, L, f));
+  return eval_g_read(S, f.N, g, mnorm);
 }
 
 // MIXED policy: switch to float64-accurate sweeps once g is within a factor K of the
@@ -497,6 +554,100 @@ static void maybe_switch(Solver& S, double g, double mnorm, double /*g_prev*/) {
     ++S.stall;
   }
   if (g < floor_est || S.stall >= 20) S.refined = true;
+}
+
+// Sweeps to run before the next exact g check: about half of the sweeps that the observed
+// per-sweep contraction predicts are left, as a power of two in [1, 32].  The iterates do not
+// depend on it; only the stopping point can move by at most that many sweeps.
+static int next_check_interval(double g, double g_prev, int k_prev, double tol) {
+  if (g_prev <= 0 || !(g > 0)) return 1;
+  const double rho = std::pow(g / g_prev, 1.0 / std::max(k_prev, 1));
+  int k;
+  if (!(rho < 1.0)) {
+    k = std::min(2 * k_prev, 32);
+  } else {
+    const double n_left = std::log(tol / g) / std::log(rho);
+    const double half = 0.5 * n_left;
+    k = 1;
+    while (k * 2 <= half && k < 32) k *= 2;
+  }
+  return std::max(1, std::min(k, 32));
+}
+
+template <typename Fn>
+static int graph_run(Solver& S, const std::string& key, Fn&& body) {
+  if (!S.use_graphs || !S.gc) return body();
+  cpmg_ctx* c = S.c;
+  auto it = S.gc->m.find(key);
+  if (it != S.gc->m.end() && it->second.z0 != S.z0) {
+    CPMG_CUDA_TRY(cudaStreamSynchronize(S.st));
+    CPMG_TRY(profile_collect(c));
+    if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+    for (auto& e : it->second.events) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    S.gc->m.erase(it);
+    it = S.gc->m.end();
+  }
+  if (it != S.gc->m.end()) {
+    CPMG_CUDA_TRY(cudaGraphLaunch(it->second.exec, S.st));
+    c->launches += it->second.dlaunch;
+    S.refine_sweeps += it->second.drefine;
+    for (auto& e : it->second.events) c->pending.push_back(e);
+    if (c->pending.size() > 4096) CPMG_TRY(profile_collect(c));
+    return CPMG_OK;
+  }
+  const int64_t l0 = c->launches;
+  const int r0 = S.refine_sweeps;
+  const size_t p0 = c->pending.size();
+  CPMG_CUDA_TRY(cudaStreamBeginCapture(S.st, cudaStreamCaptureModeThreadLocal));
+  c->capturing = true;
+  int st = body();
+  c->capturing = false;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(S.st, &g);
+  GraphEntry e;
+  e.events.assign(c->pending.begin() + p0, c->pending.end());
+  c->pending.resize(p0);
+  cudaError_t ie = cudaSuccess;
+  if (st == CPMG_OK && ce == cudaSuccess && g) ie = cudaGraphInstantiate(&e.exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (st != CPMG_OK || ce != cudaSuccess || !g || ie != cudaSuccess) {
+    for (auto& ev : e.events) {
+      cudaEventDestroy(ev.a);
+      cudaEventDestroy(ev.b);
+    }
+    if (st != CPMG_OK) {
+      cudaGetLastError();
+      return st;
+    }
+    set_last_error(ce != cudaSuccess ? ce : ie, "graph capture", __FILE__, __LINE__);
+    cudaGetLastError();
+    return CPMG_CUDA_ERROR;
+  }
+  e.z0 = S.z0;
+  e.dlaunch = c->launches - l0;
+  e.drefine = S.refine_sweeps - r0;
+  CPMG_CUDA_TRY(cudaGraphLaunch(e.exec, S.st));
+  for (auto& ev : e.events) c->pending.push_back(ev);
+  S.gc->m[key] = std::move(e);
+  return CPMG_OK;
+}
+
+// Plans (and scratch sized for them) for every MTTKRP a solve can issue, so that nothing is
+// planned or allocated while a graph is being captured.
+static int preplan(cpmg_ctx* c, const std::vector<const Level*>& levels, int R) {
+  size_t part = 0, tab = 0;
+  for (const Level* L : levels)
+    for (int n = 0; n < L->s.N; ++n)
+      for (int prec : {(int)P_FP32, (int)P_FP64, (int)P_DF}) {
+        const MttkrpPlan* p = nullptr;
+        CPMG_TRY(get_plan(c, L->s, n, R, prec, L->dtype, L->Z, &p));
+        part = std::max(part, p->partial_bytes());
+        tab = std::max(tab, p->tables_bytes());
+      }
+  return ensure_scratch(c, part, tab);
 }
 
 static int tensor_norm(Solver& S, const Level& L, FactorSet& f, double* znorm) {
@@ -719,6 +870,8 @@ static double now_s() {
 
 static Solver make_solver(cpmg_ctx* c, const cpmg_opts* o) {
   Solver S{c, *o, c->stream, o->precision};
+  // stream capture is not available on the legacy default stream
+  S.use_graphs = o->use_graphs != 0 && c->stream != nullptr;
   return S;
 }
 
@@ -753,6 +906,7 @@ void cpmg_opts_default(cpmg_opts* o) {
   o->als_fallback = 0;
   o->mixed_switch = 64.0;
   o->check_every = 1;
+  o->use_graphs = 1;
 }
 
 const char* cpmg_status_str(int s) {
@@ -784,6 +938,7 @@ int cpmg_create(cpmg_ctx** out, int device, size_t budget, void* stream) {
     c->num_sms = sms;
   int st = dalloc_t(c, &c->dsc, 4096);
   if (st == CPMG_OK) st = dalloc_t(c, &c->dstatus, 64);
+  if (st == CPMG_OK) st = dalloc_t(c, &c->gscratch, (size_t)kFuseMaxBlocks * kMaxRank * (kMaxRank + 1) / 2);
   if (st == CPMG_OK && cudaMallocHost(&c->hsc, 4096 * sizeof(double)) != cudaSuccess) st = CPMG_CUDA_ERROR;
   if (st == CPMG_OK && cudaMemsetAsync(c->dsc, 0, 4096 * sizeof(double), c->stream) != cudaSuccess)
     st = CPMG_CUDA_ERROR;
@@ -958,18 +1113,37 @@ int cp_als_sweep(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A, int
   double z2 = 0, fv = 0, g = -1, gprev = -1, mn = 0;
   int done = 0;
   bool conv = false;
+  GraphCache gc;  // graphs of this call only
+  S.gc = &gc;
+  S.z0 = L.Z;
   if (st == CPMG_OK) st = tensor_norm(S, L, fs, &S.znorm);
-  for (int it = 0; st == CPMG_OK && it < nsweeps; ++it) {
-    st = als_sweep(S, L, 0, fs);
-    done = it + 1;
-    if (st == CPMG_OK && opts->check_every > 0 && done % opts->check_every == 0) {
-      st = eval_g(S, L, fs, &g, &mn);
+  if (st == CPMG_OK) st = preplan(c, {&L}, R);
+  // check_every > 0: exact g every check_every sweeps; check_every < 0: adaptive interval
+  int k = opts->check_every > 0 ? opts->check_every : 1;
+  while (st == CPMG_OK && done < nsweeps) {
+    const bool check = opts->check_every != 0;
+    const int kk = check ? std::min(k, nsweeps - done) : 1;
+    const std::string key = "als" + std::to_string(kk) + (check ? "+g|" : "|") + (S.refined ? "r" : "f");
+    st = graph_run(S, key, [&]() -> int {
+      for (int j = 0; j < kk; ++j) CPMG_TRY(als_sweep(S, L, 0, fs));
+      if (check) CPMG_TRY(eval_g_launch(S, L, fs));
+      return CPMG_OK;
+    });
+    done += kk;
+    if (st == CPMG_OK && check) {
+      st = eval_g_read(S, fs.N, &g, &mn);
       if (st != CPMG_OK) break;
       if (g < opts->tol) { conv = true; break; }
+      const bool was_refined = S.refined;
       maybe_switch(S, g, mn, gprev);
+      if (opts->check_every < 0) k = (S.refined != was_refined) ? 1 : next_check_interval(g, gprev, kk, opts->tol);
       gprev = g;
     }
   }
+  if (st == CPMG_OK) st = cudaStreamSynchronize(c->stream) == cudaSuccess ? CPMG_OK : CPMG_CUDA_ERROR;
+  S.gc = nullptr;
+  profile_collect(c);
+  gc.clear();
   if (st == CPMG_OK) st = launch_sort(fs, S.sortbuf, c->stream);
   if (st == CPMG_OK) st = eval_f(S, L, fs, &fv, &z2);
   if (st == CPMG_OK) st = eval_g(S, L, fs, &g, nullptr);
@@ -985,7 +1159,7 @@ int cp_als_sweep(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A, int
     res->seconds = now_s() - t0;
   }
   if (st == CPMG_OK && (!std::isfinite(fv) || !std::isfinite(g))) st = CPMG_NUMERIC;
-  if (st == CPMG_OK && opts->check_every > 0 && !conv && !(g < opts->tol)) st = CPMG_NOT_CONVERGED;
+  if (st == CPMG_OK && opts->check_every != 0 && !conv && !(g < opts->tol)) st = CPMG_NOT_CONVERGED;
   if (res) res->status = st;
   dfree(c, L.M);
   dfree(c, S.sortbuf);
@@ -999,10 +1173,14 @@ static int setup_cycles(Solver& S, cpmg_hier* h, int* cycles, std::vector<double
   double g_prev = -1.0;
   *cycles = 0;
   for (int cycle = 1; cycle <= S.o.max_setup_cycles; ++cycle) {
-    CPMG_TRY(amg_mult(S, h, 0, cycle == 1, true, true));
+    const std::string key = std::string("setup|") + (cycle == 1 ? "1|" : "n|") + (S.refined ? "r" : "f");
+    CPMG_TRY(graph_run(S, key, [&]() -> int {
+      CPMG_TRY(amg_mult(S, h, 0, cycle == 1, true, true));
+      return eval_g_launch(S, h->L[0], h->L[0].A);
+    }));
     *cycles = cycle;
     double g = 0, mn = 0;
-    CPMG_TRY(eval_g(S, h->L[0], h->L[0].A, &g, &mn));
+    CPMG_TRY(eval_g_read(S, h->N, &g, &mn));
     hist->push_back(g);
     if (g < S.o.tol) break;
     if (cycle >= 3 && g > (1.0 - S.o.stag_eps) * g_prev) break;
@@ -1010,6 +1188,12 @@ static int setup_cycles(Solver& S, cpmg_hier* h, int* cycles, std::vector<double
     g_prev = g;
   }
   return CPMG_OK;
+}
+
+static int hier_preplan(cpmg_ctx* c, cpmg_hier* h) {
+  std::vector<const Level*> lv;
+  for (auto& L : h->L) lv.push_back(&L);
+  return preplan(c, lv, h->R);
 }
 
 int mg_setup(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A_boot, double* const* A_test,
@@ -1034,6 +1218,9 @@ int mg_setup(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A_boot, do
   if (st == CPMG_OK) st = factors_in(c, Z->mem, A_boot, L0.A);
   for (int t = 0; st == CPMG_OK && t < h->nt; ++t) st = factors_in(c, Z->mem, A_test + (size_t)t * Z->N, L0.tf[t]);
   if (st == CPMG_OK) st = tensor_norm(S, L0, L0.A, &S.znorm);
+  S.gc = &h->graphs;
+  S.z0 = L0.Z;
+  if (st == CPMG_OK) st = hier_preplan(c, h);
   int cycles = 0;
   std::vector<double> hist;
   if (st == CPMG_OK) st = setup_cycles(S, h, &cycles, &hist);
@@ -1069,34 +1256,49 @@ static int solve_cycles(Solver& S, cpmg_hier* h, int cycles_done, int* solve, in
                         double* g_out) {
   Level& L0 = h->L[0];
   double g_old = 0, mn = 0;
-  CPMG_TRY(eval_g(S, L0, L0.A, &g_old, &mn));
+  CPMG_TRY(graph_run(S, std::string("g|") + (S.refined ? "r" : "f"),
+                     [&]() -> int { return eval_g_launch(S, L0, L0.A); }));
+  CPMG_TRY(eval_g_read(S, h->N, &g_old, &mn));
   maybe_switch(S, g_old, mn, -1.0);
   *solve = 0;
   *restarted = 0;
   *als_iters = 0;
   while (g_old >= S.o.tol && cycles_done + *solve < S.o.max_cycles) {
-    CPMG_TRY(fs_copy(h->Aprev, L0.A, S.st));
-    CPMG_TRY(cp_fas(S, h, 0, false, 0));
+    CPMG_TRY(graph_run(S, std::string("fas|") + (S.refined ? "r" : "f"), [&]() -> int {
+      CPMG_TRY(fs_copy(h->Aprev, L0.A, S.st));
+      CPMG_TRY(cp_fas(S, h, 0, false, 0));
+      return eval_g_launch(S, L0, L0.A);
+    }));
     *solve += 1;
     double g_new = 0;
-    CPMG_TRY(eval_g(S, L0, L0.A, &g_new, &mn));
+    CPMG_TRY(eval_g_read(S, h->N, &g_new, &mn));
     if (*solve > 5 && g_new >= g_old) {
       if (!*restarted) {
         *restarted = 1;
-        CPMG_TRY(fs_copy(L0.A, h->Aprev, S.st));
-        CPMG_TRY(amg_mult(S, h, 0, false, false, false));  // down-sweep, boot factors frozen
+        // discard the new iterate; rebuild the operators by a down-sweep, boot factors frozen
+        CPMG_TRY(graph_run(S, std::string("down|") + (S.refined ? "r" : "f"), [&]() -> int {
+          CPMG_TRY(fs_copy(L0.A, h->Aprev, S.st));
+          return amg_mult(S, h, 0, false, false, false);
+        }));
         continue;
       }
       if (S.o.als_fallback) {
         CPMG_TRY(fs_copy(L0.A, h->Aprev, S.st));
-        double g = g_old, gp = -1;
-        int it = 0;
+        double g = g_old, gp = -1.0;
+        int it = 0, k = 1;
         while (it < S.o.max_als_iters && g >= S.o.tol) {
-          CPMG_TRY(als_sweep(S, L0, 0, L0.A));
-          ++it;
-          CPMG_TRY(eval_g(S, L0, L0.A, &g, &mn));
-          maybe_switch(S, g, mn, gp);
+          k = std::min(k, S.o.max_als_iters - it);
+          const int kk = k;
+          CPMG_TRY(graph_run(S, "als" + std::to_string(kk) + "+g|" + (S.refined ? "r" : "f"), [&]() -> int {
+            for (int j = 0; j < kk; ++j) CPMG_TRY(als_sweep(S, L0, 0, L0.A));
+            return eval_g_launch(S, L0, L0.A);
+          }));
+          it += kk;
           gp = g;
+          CPMG_TRY(eval_g_read(S, h->N, &g, &mn));
+          const bool was_refined = S.refined;
+          maybe_switch(S, g, mn, -1.0);
+          k = (S.refined != was_refined) ? 1 : next_check_interval(g, gp, kk, S.o.tol);
         }
         CPMG_TRY(launch_sort(L0.A, S.sortbuf, S.st));
         *als_iters = it;
@@ -1130,6 +1332,9 @@ int mg_fas_solve(cpmg_ctx* c, cpmg_hier* h, const cpmg_tensor* Z, double* const*
   c->prof_Z = L0.Z;
   if (st == CPMG_OK) st = factors_in(c, Z->mem, A, L0.A);
   if (st == CPMG_OK) st = tensor_norm(S, L0, L0.A, &S.znorm);
+  S.gc = &h->graphs;
+  S.z0 = L0.Z;
+  if (st == CPMG_OK) st = hier_preplan(c, h);
   int solve = 0, restarted = 0, als_it = 0;
   double g = -1, fv = 0;
   if (st == CPMG_OK) st = solve_cycles(S, h, 0, &solve, &restarted, &als_it, &g);
@@ -1203,6 +1408,9 @@ int cpmg_decompose(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A, d
   if (st == CPMG_OK) st = factors_in(c, Z->mem, A, L0.A);
   for (int t = 0; st == CPMG_OK && t < h->nt; ++t) st = factors_in(c, Z->mem, A_test + (size_t)t * Z->N, L0.tf[t]);
   if (st == CPMG_OK) st = tensor_norm(S, L0, L0.A, &S.znorm);
+  S.gc = &h->graphs;
+  S.z0 = L0.Z;
+  if (st == CPMG_OK) st = hier_preplan(c, h);
   int cycles = 0, solve = 0, restarted = 0, als_it = 0;
   std::vector<double> hist;
   double g = -1, fv = 0;

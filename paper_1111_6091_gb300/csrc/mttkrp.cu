@@ -1022,7 +1022,9 @@ int mttkrp_plan(const Shape& s, int mode, int R, int prec, int zdtype, const voi
 
 int mttkrp_run(const MttkrpPlan& p, const Shape& s, const void* Z, const double* const* A,
                const MttkrpScratch& w, double* M, cudaStream_t st, cudaEvent_t ev0,
-               cudaEvent_t ev1, int* err) {
+               cudaEvent_t ev1, int* err, bool finish, bool ev_external) {
+  // inside a stream capture, only an "external" event record becomes a node that fires on replay
+  const unsigned evflags = ev_external ? cudaEventRecordExternal : cudaEventRecordDefault;
   // tables: Kin / Kout for the register-load kernel, the full row table W for the TMA kernel
   char* tb = reinterpret_cast<char*>(w.tables);
   void* kin = nullptr;
@@ -1081,7 +1083,7 @@ int mttkrp_run(const MttkrpPlan& p, const Shape& s, const void* Z, const double*
   ma.kin = kin;
   ma.kout = kout;
   ma.partial = w.partial;
-  if (ev0) CPMG_CUDA_TRY(cudaEventRecord(ev0, st));
+  if (ev0) CPMG_CUDA_TRY(cudaEventRecordWithFlags(ev0, st, evflags));
   if (p.use_tma) {
     TmaArgs ta;
     ta.m = ma;
@@ -1127,7 +1129,8 @@ int mttkrp_run(const MttkrpPlan& p, const Shape& s, const void* Z, const double*
       return CPMG_CUDA_ERROR;
     }
   }
-  if (ev1) CPMG_CUDA_TRY(cudaEventRecord(ev1, st));
+  if (ev1) CPMG_CUDA_TRY(cudaEventRecordWithFlags(ev1, st, evflags));
+  if (!finish) return CPMG_OK;
   FinishArgs fa;
   fa.partial = w.partial;
   fa.rows = (p.mode == 0) ? p.I1 : p.In;

@@ -55,6 +55,6 @@ struct MttkrpScratch {
 // kernel and the ordered reduction into M (float64, I_n x R column-major).
 int mttkrp_run(const MttkrpPlan& p, const Shape& s, const void* Z, const double* const* A_dev_ptrs,
                const MttkrpScratch& w, double* M, cudaStream_t st, cudaEvent_t ev0 = nullptr,
-               cudaEvent_t ev1 = nullptr, int* err = nullptr);
+               cudaEvent_t ev1 = nullptr, int* err = nullptr, bool finish = true, bool ev_external = false);
 
 }  // namespace cpmg

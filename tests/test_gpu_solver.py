@@ -156,3 +156,30 @@ def test_host_buffers_roundtrip(cpmg_ctx):
     cpmg.cpmg_decompose(cpmg_ctx, cpmg.colmajor(p.Z, device="cpu", pin=True), Ah, tfh, **kw)
     for a, b in zip(host(cpmg, A), host(cpmg, Ah)):
         assert np.array_equal(a, b)
+
+
+def test_graph_replay_matches_eager(cpmg_ctx):
+    """The same solve with CUDA-graph replay (context on a dedicated stream) and without graphs
+    gives bitwise identical factors: the graphs only change how launches are issued."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((32, 30, 28), 3, congruence=0.5, eta_homo=0.001, dtype=np.float32, seed=4)
+    outs = []
+    for graphs in (0, 1):
+        stream = torch.cuda.Stream()
+        ctx = cpmg.Context(0, stream=stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            A = dev(cpmg, p.A0)
+            tf = [dev(cpmg, b) for b in p.tfms]
+            r = cpmg.cpmg_decompose(ctx, cpmg.colmajor(p.Z), A, tf, precision=cpmg.PREC_MIXED, tol=1e-7,
+                                    coarsest=(8, 8, 8), als_fallback=1, use_graphs=graphs)
+            B = dev(cpmg, p.A0)
+            cpmg.cp_als_sweep(ctx, cpmg.colmajor(p.Z), B, 40, precision=cpmg.PREC_MIXED, check_every=5,
+                              use_graphs=graphs)
+            stream.synchronize()
+        outs.append(([cpmg.to_numpy(a) for a in A], [cpmg.to_numpy(b) for b in B], r))
+        ctx.close()
+    (A0, B0, r0), (A1, B1, r1) = outs
+    assert r0["iters_setup"] == r1["iters_setup"] and r0["iters_solve"] == r1["iters_solve"]
+    for a, b in zip(A0 + B0, A1 + B1):
+        assert np.array_equal(a, b)
