@@ -269,6 +269,7 @@ def run_gpu(args):
         ms4, n4, b4 = ctx.profile_read(0)
         ctx.profile(False)
     gbs4 = b4 / (ms4 * 1e-3 / n4) / 1e9
+    ttm4 = ttm_400cubed(ctx, stream, Z4, hbm, how)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -295,6 +296,7 @@ def run_gpu(args):
                              "L2-resident inside a solve; frac is against HBM"},
         "mttkrp_400cubed_fp32": {"achieved": gbs4, "peak": hbm, "unit": "GB/s", "frac": gbs4 / hbm,
                                  "avg_us": ms4 * 1e3 / n4, "launches": n4, "peak_source": how},
+        "ttm_400cubed_tc": ttm4,
         "cpu_baseline": cpu,
         "gpu_launches": int(launches),
         "gpu_launches_note": "kernel launches per step issued by libcpmg (graph replays count their kernels)",
@@ -308,6 +310,69 @@ def run_gpu(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+TTM_DIMS, TTM_IC = (400, 400, 400), 200
+
+
+def ttm_rhat(seed=3):
+    import torch
+    rng = np.random.default_rng(seed)
+    return [torch.from_numpy(np.ascontiguousarray(rng.standard_normal((TTM_IC, I)).T)).cuda() for I in TTM_DIMS]
+
+
+def ttm_400cubed(ctx, stream, Z4, hbm, how, reps=5):
+    """Level-0 restriction of the 400^3 float tensor (modes 400 -> 200 in turn) on tcgen05 in
+    split BF16: per-launch CUDA events around the three mode-product kernels."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    with torch.cuda.stream(stream):
+        Rh = ttm_rhat()
+        for _ in range(2):
+            cpmg.cpmg_ttm(ctx, Z4, Rh, tensor_cores=1)
+        ctx.profile(True)
+        ctx.profile_reset()
+        for _ in range(reps):
+            cpmg.cpmg_ttm(ctx, Z4, Rh, tensor_cores=1)
+        ms, n, bpl = ctx.profile_read(3)
+        ctx.profile(False)
+    I, c = TTM_DIMS[0], TTM_IC
+    # useful flops of the three mode products, and the bytes each reads and writes once
+    flops = 2.0 * c * I * (I * I) + 2.0 * c * I * (c * I) + 2.0 * c * I * (c * c)
+    byts = 4.0 * (I ** 3 + c * I * I) + 4.0 * (c * I * I + c * c * I) + 4.0 * (c * c * I + c ** 3)
+    t = ms * 1e-3 / reps
+    npad = -(-c // 16) * 16
+    tc_peak = peaks_tensor()
+    return {"kernel": "ttm_tc (3 mode products 400->200, split BF16, FP32 accumulate)",
+            "avg_us_per_restriction": t * 1e6, "launches": n,
+            "achieved_gbs": byts / t / 1e9, "hbm_peak": hbm, "hbm_frac": byts / t / 1e9 / hbm,
+            "useful_tflops": flops / t / 1e12,
+            "tensor_tflops_issued": 3 * flops * npad / c / t / 1e12,
+            "bf16_peak_tflops": tc_peak, "tensor_frac": 3 * flops * npad / c / t / 1e12 / tc_peak if tc_peak else None,
+            "algorithmic_bytes": byts, "algorithmic_flops": flops, "peak_source": how}
+
+
+def peaks_tensor():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d.get("bf16_tflops") or 0) or None
+    except Exception:
+        return 1900.0  # fallback burst figure
+
+
+def run_ttm_case(args):
+    """Small case for profiler captures: one level-0 restriction of the 400^3 float tensor on
+    tensor cores (three k_ttm_tc launches)."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    rng = np.random.default_rng(23)
+    Zn = np.asfortranarray(rng.standard_normal(TTM_DIMS).astype(np.float32))
+    ctx = cpmg.Context(0)
+    Y = cpmg.cpmg_ttm(ctx, cpmg.colmajor(Zn), ttm_rhat(), tensor_cores=1)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "ttm 400^3 -> 200^3 tensor cores", "y00": float(Y.flatten()[0])}))
+    ctx.close()
 
 
 def run_mttkrp_case(args):
@@ -330,6 +395,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--mttkrp-case", action="store_true", help="profiler case: 2 sweeps at 400^3")
     ap.add_argument("--case-prec", default="fp32", choices=["fp32", "df", "fp64"])
+    ap.add_argument("--ttm-case", action="store_true", help="profiler case: one 400^3 restriction")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -341,6 +407,8 @@ def main():
         build.build()
     if args.mttkrp_case:
         run_mttkrp_case(args)
+    elif args.ttm_case:
+        run_ttm_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

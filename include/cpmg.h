@@ -106,6 +106,10 @@ typedef struct {
                                         adaptive interval, at most 32, from the observed rate)  */
   int use_graphs;                    /* 1: capture sweeps / cycles as CUDA graphs and replay
                                         (needs a context stream other than the legacy default) */
+  int ttm_tensor_cores;              /* 1: restriction of float tensors on tcgen05 tensor cores
+                                        in split BF16 (3 products, FP32 accumulation); 0: FP32
+                                        CUDA cores.  The coarse tensors only shape the FAS
+                                        corrections, so either keeps the fine-level fixed point */
 } cpmg_opts;
 
 typedef struct {
@@ -148,7 +152,10 @@ int cpmg_mttkrp(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, const double* const*
 /* Y = Z x_{n : Rhat[n] != NULL} Rhat^(n), the restriction of Eq. ctensor_transformed applied
  * one mode at a time in increasing n.  Rhat[n] is a device float64 Ic_n x I_n column-major
  * matrix or NULL (mode not coarsened).  Y is a device tensor of Z's dtype with the coarse
- * sizes, column-major.  tensor_cores: 0 = FP32/FP64 CUDA-core GEMM, 1 = tcgen05 (float Z). */
+ * sizes, column-major.  tensor_cores: 0 = CUDA-core GEMM in Z's type; 1 = tcgen05 tensor cores
+ * in split BF16 (x = hi + lo, products hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor
+ * memory; relative error near 2^-16 of sum |Rhat||Z|), float Z only, Ic_n <= 256, else
+ * CPMG_UNSUPPORTED.  CPMG_TIMEOUT if a bounded device-side wait expired. */
 int cpmg_ttm(cpmg_ctx* ctx, const cpmg_tensor* Z, const double* const* Rhat, const int64_t* Ic,
              int tensor_cores, void* Y);
 
@@ -217,7 +224,9 @@ int cpmg_decompose(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A,
 /* Per-kernel timing: when enabled, each launch of the finest-level MTTKRP main kernel is
  * bracketed by CUDA events on the context's stream; the statistics accumulate until reset.
  * kind: 0 = FP32 launches, 1 = float64-accurate (pairs of floats), 2 = FP64.  bytes_per_launch
- * is the algorithmic traffic: sizeof(z) * prod(I) + 4 R sum_n I_n. */
+ * is the algorithmic traffic: sizeof(z) * prod(I) + 4 R sum_n I_n.  kind 3 = the tensor-core
+ * mode products of the restriction (finest level in the solvers, every one in cpmg_ttm), with
+ * bytes_per_launch = 4 (numel in + numel out). */
 int cpmg_profile_enable(cpmg_ctx* ctx, int enable);
 int cpmg_profile_read(cpmg_ctx* ctx, int kind, double* total_ms, int64_t* launches,
                       double* bytes_per_launch);

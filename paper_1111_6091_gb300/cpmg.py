@@ -42,7 +42,8 @@ class cpmg_opts(C.Structure):
                 ("nuc_setup", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("nuc", C.c_int),
                 ("n_t", C.c_int), ("max_setup_cycles", C.c_int), ("stag_eps", C.c_double),
                 ("gs_sweeps", C.c_int), ("coarsest", C.c_int64 * MAX_MODES), ("als_fallback", C.c_int),
-                ("mixed_switch", C.c_double), ("check_every", C.c_int), ("use_graphs", C.c_int)]
+                ("mixed_switch", C.c_double), ("check_every", C.c_int), ("use_graphs", C.c_int),
+                ("ttm_tensor_cores", C.c_int)]
 
 
 class cpmg_result(C.Structure):

@@ -25,7 +25,8 @@ using namespace cpmg;
 struct ProfEvents {
   cudaEvent_t a, b;
   double bytes;
-  int kind;     // 0: FP32, 1: pairs of floats, 2: FP64 finest-level MTTKRP main kernel
+  int kind;     // 0: FP32, 1: pairs of floats, 2: FP64 finest-level MTTKRP main kernel;
+                // 3: tensor-core mode product of the restriction
   bool owned;   // recorded inside a CUDA graph: the graph keeps the events
 };
 
@@ -51,9 +52,9 @@ struct cpmg_ctx {
   bool profile = false;
   std::vector<ProfEvents> pending;
   std::vector<ProfEvents> pool;
-  double prof_ms[3] = {0, 0, 0};
-  int64_t prof_launches[3] = {0, 0, 0};
-  double prof_bytes[3] = {0, 0, 0};
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_launches[4] = {0, 0, 0, 0};
+  double prof_bytes[4] = {0, 0, 0, 0};
   int64_t launches = 0;
   const void* prof_Z = nullptr;  // tensor whose MTTKRPs are profiled (the finest level)
   bool capturing = false;        // a CUDA graph capture is open on `stream`
@@ -232,6 +233,43 @@ struct GraphCache {
   }
 };
 
+// A pair of timing events for one profiled launch (from the pool, or new and owned by the graph
+// being captured), queued for profile_collect.
+static int prof_events(cpmg_ctx* c, int kind, double bytes, cudaEvent_t* e0, cudaEvent_t* e1) {
+  ProfEvents pe;
+  if (!c->pool.empty() && !c->capturing) {
+    pe = c->pool.back();
+    c->pool.pop_back();
+  } else {
+    CPMG_CUDA_TRY(cudaEventCreate(&pe.a));
+    CPMG_CUDA_TRY(cudaEventCreate(&pe.b));
+  }
+  pe.bytes = bytes;
+  pe.owned = c->capturing;
+  pe.kind = kind;
+  c->pending.push_back(pe);
+  *e0 = pe.a;
+  *e1 = pe.b;
+  return CPMG_OK;
+}
+
+// Events for the tensor-core mode products of one restriction (2 per coarsened mode that runs
+// on tcgen05), with the algorithmic bytes of each (float in + float out).
+static int prof_ttm(cpmg_ctx* c, const Shape& s, int dtype, const double* const* Rh, const int64_t* Ic,
+                    int tensor_cores, cudaEvent_t* ev) {
+  for (int k = 0; k < 2 * kMaxModes; ++k) ev[k] = nullptr;
+  if (!c->profile || !tensor_cores || dtype != CPMG_F32) return CPMG_OK;
+  Shape cur = s;
+  for (int n = 0; n < s.N; ++n) {
+    if (!Rh[n]) continue;
+    const double in = 4.0 * (double)cur.numel();
+    const bool tc = ttm_tc_supported(cur, dtype, n, Ic[n]);
+    cur.dims[n] = Ic[n];
+    if (tc) CPMG_TRY(prof_events(c, 3, in + 4.0 * (double)cur.numel(), &ev[2 * n], &ev[2 * n + 1]));
+  }
+  return CPMG_OK;
+}
+
 // kind < 0: M = MTTKRP (reduced by the finish kernel).  kind 0 / 1: the MTTKRP followed by the
 // fused reduction + ALS solve / Gauss-Seidel (with right-hand side F) + Gram refresh of mode n.
 static int run_mttkrp_k(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, const FactorSet& f, int mode,
@@ -251,22 +289,9 @@ static int run_mttkrp_k(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, c
   w.partial = c->mt_partial;
   w.tables = c->mt_tables;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->profile && Z == c->prof_Z) {
-    ProfEvents pe;
-    if (!c->pool.empty() && !c->capturing) {
-      pe = c->pool.back();
-      c->pool.pop_back();
-    } else {
-      CPMG_CUDA_TRY(cudaEventCreate(&pe.a));
-      CPMG_CUDA_TRY(cudaEventCreate(&pe.b));
-    }
-    pe.bytes = algorithmic_bytes(s, mode, f.R, dtype);
-    pe.owned = c->capturing;
-    pe.kind = p->prec == P_FP32 ? 0 : (p->prec == P_DF ? 1 : 2);
-    c->pending.push_back(pe);
-    e0 = pe.a;
-    e1 = pe.b;
-  }
+  if (c->profile && Z == c->prof_Z)
+    CPMG_TRY(prof_events(c, p->prec == P_FP32 ? 0 : (p->prec == P_DF ? 1 : 2), algorithmic_bytes(s, mode, f.R, dtype),
+                         &e0, &e1));
   const double* Aptrs[kMaxModes];
   for (int m = 0; m < kMaxModes; ++m) Aptrs[m] = f.A[m];
   CPMG_TRY(mttkrp_run(*p, s, Z, Aptrs, w, M, c->stream, e0, e1, c->dstatus + 1, kind < 0, c->capturing));
@@ -312,6 +337,7 @@ struct cpmg_hier {
   double* Aold = nullptr;  // backing of a FactorSet copy for the restart rule
   FactorSet Aprev;
   int ttm_tc = 0;
+  void* tcs = nullptr;     // split R-hat operand of the tensor-core restriction
   GraphCache graphs;
 };
 
@@ -371,6 +397,7 @@ static void hier_destroy(cpmg_hier* h) {
   for (auto& L : h->L) level_free(c, L);
   dfree(c, h->tmp0);
   dfree(c, h->tmp1);
+  dfree(c, h->tcs);
   dfree(c, h->sortbuf);
   fs_free(c, &h->Aprev);
   delete h;
@@ -425,6 +452,11 @@ static int hier_build(cpmg_ctx* c, const Shape& s0, int dtype, int R, const cpmg
   }
   if (st == CPMG_OK) st = dalloc(c, &h->tmp0, tmpb);
   if (st == CPMG_OK) st = dalloc(c, &h->tmp1, tmpb);
+  if (st == CPMG_OK && dtype == CPMG_F32 && o->ttm_tensor_cores) {
+    int64_t imax = 1;
+    for (int n = 0; n < s0.N; ++n) imax = std::max(imax, s0.dims[n]);
+    st = dalloc(c, &h->tcs, ttm_tc_scratch_bytes(imax));
+  }
   if (st == CPMG_OK) st = dalloc_t(c, &h->sortbuf, sortn);
   if (st == CPMG_OK) st = fs_alloc(c, &h->Aprev, s0.N, R, s0.dims);
   if (st != CPMG_OK) {
@@ -743,7 +775,11 @@ static int amg_mult(Solver& S, cpmg_hier* h, int lvl, bool first, bool relax_boo
     for (int t = 0; t < h->nt; ++t) CPMG_TRY(restrict_set(S, L, L.tf[t], C.tf[t]));
     const double* Rh[kMaxModes];
     for (int n = 0; n < kMaxModes; ++n) Rh[n] = (n < L.s.N && L.co[n]) ? L.Rhat[n] : nullptr;
-    CPMG_TRY(ttm_restrict(L.s, L.Z, L.dtype, Rh, L.cd, const_cast<void*>(C.Z), h->tmp0, h->tmp1, S.ttm_tc, S.st));
+    const int tc = h->tcs ? S.ttm_tc : 0;
+    cudaEvent_t ev[2 * kMaxModes];
+    CPMG_TRY(prof_ttm(S.c, L.s, L.dtype, Rh, L.cd, L.Z == S.c->prof_Z ? tc : 0, ev));
+    CPMG_TRY(ttm_restrict(L.s, L.Z, L.dtype, Rh, L.cd, const_cast<void*>(C.Z), h->tmp0, h->tmp1, tc, h->tcs,
+                          S.c->dstatus + 1, ev, S.c->capturing, S.st));
     S.c->launches += 3;
     CPMG_TRY(amg_mult(S, h, lvl + 1, first, relax_boot, upsweep));
     if (upsweep) {
@@ -872,6 +908,7 @@ static Solver make_solver(cpmg_ctx* c, const cpmg_opts* o) {
   Solver S{c, *o, c->stream, o->precision};
   // stream capture is not available on the legacy default stream
   S.use_graphs = o->use_graphs != 0 && c->stream != nullptr;
+  S.ttm_tc = o->ttm_tensor_cores ? 1 : 0;
   return S;
 }
 
@@ -907,6 +944,7 @@ void cpmg_opts_default(cpmg_opts* o) {
   o->mixed_switch = 64.0;
   o->check_every = 1;
   o->use_graphs = 1;
+  o->ttm_tensor_cores = 1;
 }
 
 const char* cpmg_status_str(int s) {
@@ -982,7 +1020,7 @@ int cpmg_profile_enable(cpmg_ctx* c, int enable) {
 }
 
 int cpmg_profile_read(cpmg_ctx* c, int kind, double* total_ms, int64_t* launches, double* bytes) {
-  if (!c || kind < 0 || kind > 2) return CPMG_INVALID_ARG;
+  if (!c || kind < 0 || kind > 3) return CPMG_INVALID_ARG;
   CPMG_TRY(profile_collect(c));
   if (total_ms) *total_ms = c->prof_ms[kind];
   if (launches) *launches = c->prof_launches[kind];
@@ -993,7 +1031,7 @@ int cpmg_profile_read(cpmg_ctx* c, int kind, double* total_ms, int64_t* launches
 int cpmg_profile_reset(cpmg_ctx* c) {
   if (!c) return CPMG_INVALID_ARG;
   CPMG_TRY(profile_collect(c));
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     c->prof_ms[k] = 0;
     c->prof_launches[k] = 0;
     c->prof_bytes[k] = 0;
@@ -1043,14 +1081,28 @@ int cpmg_ttm(cpmg_ctx* c, const cpmg_tensor* Z, const double* const* Rhat, const
     icv[n] = n < s.N ? Ic[n] : 0;
     if (Rh[n] && icv[n] < 1) return CPMG_INVALID_ARG;
   }
+  if (tensor_cores && Z->dtype != CPMG_F32) return CPMG_UNSUPPORTED;
   const size_t tb = ttm_max_intermediate(s, Z->dtype, Rh, icv);
-  void *t0 = nullptr, *t1 = nullptr;
+  int64_t imax = 1;
+  for (int n = 0; n < s.N; ++n) imax = std::max(imax, s.dims[n]);
+  void *t0 = nullptr, *t1 = nullptr, *tcs = nullptr;
   int st = dalloc(c, &t0, tb);
   if (st == CPMG_OK) st = dalloc(c, &t1, tb);
-  if (st == CPMG_OK) st = ttm_restrict(s, Z->data, Z->dtype, Rh, icv, Y, t0, t1, tensor_cores, c->stream);
+  if (st == CPMG_OK && tensor_cores) st = dalloc(c, &tcs, ttm_tc_scratch_bytes(imax));
+  cudaEvent_t ev[2 * kMaxModes];
+  if (st == CPMG_OK) st = prof_ttm(c, s, Z->dtype, Rh, icv, tensor_cores, ev);
+  if (st == CPMG_OK)
+    st = ttm_restrict(s, Z->data, Z->dtype, Rh, icv, Y, t0, t1, tensor_cores ? 2 : 0, tcs, c->dstatus + 1, ev,
+                      false, c->stream);
   if (st == CPMG_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = CPMG_CUDA_ERROR;
+  if (st == CPMG_OK) {
+    int dflag = 0;
+    if (cudaMemcpy(&dflag, c->dstatus + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) st = CPMG_CUDA_ERROR;
+    else if (dflag) st = CPMG_TIMEOUT;
+  }
   dfree(c, t0);
   dfree(c, t1);
+  dfree(c, tcs);
   return st;
 }
 

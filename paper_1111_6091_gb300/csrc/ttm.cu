@@ -90,9 +90,15 @@ static void mode_geometry(const Shape& s, int mode, int64_t* L, int64_t* G) {
 }
 
 int ttm_mode(const Shape& s, const void* Z, int dtype, int mode, const double* Rh, int64_t Ic, void* Y,
-             int tensor_cores, cudaStream_t st) {
-  if (tensor_cores && dtype == CPMG_F32 && ttm_tc_supported(s, dtype, mode, Ic))
-    return ttm_mode_tc(s, reinterpret_cast<const float*>(Z), mode, Rh, Ic, reinterpret_cast<float*>(Y), st);
+             int tensor_cores, void* tc_scratch, int* err, cudaEvent_t ev0, cudaEvent_t ev1, bool ev_external,
+             cudaStream_t st) {
+  if (tensor_cores) {
+    int r = CPMG_UNSUPPORTED;
+    if (dtype == CPMG_F32 && tc_scratch && ttm_tc_supported(s, dtype, mode, Ic))
+      r = ttm_mode_tc(s, reinterpret_cast<const float*>(Z), mode, Rh, Ic, reinterpret_cast<float*>(Y), tc_scratch,
+                      err, ev0, ev1, ev_external, st);
+    if (r != CPMG_UNSUPPORTED || tensor_cores == 2) return r;
+  }
   int64_t L, G;
   mode_geometry(s, mode, &L, &G);
   const int64_t In = s.dims[mode];
@@ -144,7 +150,8 @@ size_t ttm_max_intermediate(const Shape& s, int dtype, const double* const* Rhat
 }
 
 int ttm_restrict(const Shape& s, const void* Z, int dtype, const double* const* Rhat, const int64_t* Ic,
-                 void* Y, void* tmp0, void* tmp1, int tensor_cores, cudaStream_t st) {
+                 void* Y, void* tmp0, void* tmp1, int tensor_cores, void* tc_scratch, int* err,
+                 const cudaEvent_t* ev, bool ev_external, cudaStream_t st) {
   int last = -1;
   for (int n = 0; n < s.N; ++n)
     if (Rhat[n]) last = n;
@@ -159,7 +166,8 @@ int ttm_restrict(const Shape& s, const void* Z, int dtype, const double* const* 
   for (int n = 0; n < s.N; ++n) {
     if (!Rhat[n]) continue;
     void* dst = (n == last) ? Y : (flip ? tmp1 : tmp0);
-    CPMG_TRY(ttm_mode(cur, src, dtype, n, Rhat[n], Ic[n], dst, tensor_cores, st));
+    CPMG_TRY(ttm_mode(cur, src, dtype, n, Rhat[n], Ic[n], dst, tensor_cores, tc_scratch, err,
+                      ev ? ev[2 * n] : nullptr, ev ? ev[2 * n + 1] : nullptr, ev_external, st));
     cur.dims[n] = Ic[n];
     src = dst;
     flip ^= 1;

@@ -102,6 +102,86 @@ def test_ttm_restrict(cpmg_ctx, dims, mask):
     assert np.all(err <= 2e-5 * scale + 1e-30)
 
 
+# split BF16 on tcgen05: x = hi + lo; hi*hi + hi*lo + lo*hi drops lo*lo and the rounding of
+# lo, each at most 2^-18 |x||y|, plus FP32 accumulation; bound per entry 1e-4 of sum |R||Z|
+# per mode product, the RMS of (error / scale) must stay under 2e-5.
+TC_CASES = [
+    ((20, 18, 16), (1, 1, 1), "rhat"),      # mode 1 tensor map, later modes direct loads
+    ((33, 7, 65), (1, 0, 1), "rhat"),       # ragged: direct loads, tile tails
+    ((64, 40, 36), (1, 1, 1), "rhat"),      # tensor maps for every mode, several tiles
+    ((9, 8, 7, 6), (1, 1, 1, 1), "rhat"),   # 4-way, direct loads
+    ((130, 70), (0, 1), "rhat"),            # last mode only, two 128-row tiles
+    ((512, 6, 5), (1, 0, 0), "dense"),      # Ic = 256: the widest accumulator
+    ((8, 400, 12), (0, 1, 0), "dense"),     # Ic = 200 (padded to 208), middle mode
+    ((200, 300, 4), (0, 1, 0), "dense"),    # Ic = 150, L = 200: tensor map, K tail of 12
+]
+
+
+@pytest.mark.parametrize("dims,mask,kind", TC_CASES)
+def test_ttm_tensor_cores(cpmg_ctx, dims, mask, kind):
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    Zn = rnd(dims, 17)
+    rng = np.random.default_rng(18)
+    Rh = []
+    for i, (I, m) in enumerate(zip(dims, mask)):
+        if not m:
+            Rh.append(None)
+        elif kind == "rhat":
+            Rh.append(rhat_for(I, 2, 8 + i))
+        else:
+            Rh.append(rng.standard_normal(((I + 1) // 2, I)))
+    Y = cpmg.cpmg_ttm(cpmg_ctx, cpmg.colmajor(Zn),
+                      [None if r is None else torch.from_numpy(np.ascontiguousarray(r.T)).cuda() for r in Rh],
+                      tensor_cores=1)
+    modes = [i for i, m in enumerate(mask) if m]
+    Z64 = Zn.astype(np.float64)
+    ref = T.ttm_modes(Z64, Rh, modes)
+    scale = T.ttm_modes(np.abs(Z64), [None if r is None else np.abs(r) for r in Rh], modes)
+    rel = np.abs(cpmg.to_numpy(Y) - ref) / scale
+    assert np.max(rel) <= 1e-4 * len(modes), float(np.max(rel))
+    assert np.sqrt(np.mean(rel ** 2)) <= 2e-5, float(np.sqrt(np.mean(rel ** 2)))
+
+
+def test_ttm_tensor_cores_unsupported(cpmg_ctx):
+    """Float64 tensors and Ic > 256 are refused on the tensor-core path, not rerouted."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    Zd = cpmg.colmajor(rnd((8, 6, 4), 1, np.float64))
+    R = torch.zeros((8, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(cpmg.CpmgError) as e:
+        cpmg.cpmg_ttm(cpmg_ctx, Zd, [R, None, None], tensor_cores=1)
+    assert e.value.status == cpmg.UNSUPPORTED
+    Zf = cpmg.colmajor(rnd((600, 3, 2), 1))
+    R = torch.zeros((600, 300), dtype=torch.float64, device="cuda")
+    with pytest.raises(cpmg.CpmgError) as e:
+        cpmg.cpmg_ttm(cpmg_ctx, Zf, [R, None, None], tensor_cores=1)
+    assert e.value.status == cpmg.UNSUPPORTED
+
+
+def test_ttm_tensor_cores_400cubed_sampled(cpmg_ctx):
+    """The level-0 restriction of the 400^3 workload (three modes 400 -> 200, the sizes the
+    solver runs), checked at sampled coarse entries the oracle computes one by one."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    dims = (400, 400, 400)
+    Zn = rnd(dims, 23)
+    rng = np.random.default_rng(24)
+    Rh = [rng.standard_normal((200, 400)) for _ in range(3)]
+    Y = cpmg.cpmg_ttm(cpmg_ctx, cpmg.colmajor(Zn),
+                      [torch.from_numpy(np.ascontiguousarray(r.T)).cuda() for r in Rh], tensor_cores=1)
+    Yh = cpmg.to_numpy(Y)
+    assert Yh.shape == (200, 200, 200)
+    Z64 = Zn.astype(np.float64)
+    Za = np.abs(Z64)
+    idx = [(0, 0, 0), (199, 199, 199), (17, 123, 5), (101, 0, 198)] + \
+          [tuple(int(v) for v in rng.integers(0, 200, 3)) for _ in range(8)]
+    for (a, b, c) in idx:
+        want = np.einsum("ijk,i,j,k->", Z64, Rh[0][a], Rh[1][b], Rh[2][c], optimize=True)
+        sc = np.einsum("ijk,i,j,k->", Za, np.abs(Rh[0][a]), np.abs(Rh[1][b]), np.abs(Rh[2][c]), optimize=True)
+        assert abs(Yh[a, b, c] - want) <= 3e-4 * sc, (a, b, c)
+
+
 def test_ttm_double_tensor(cpmg_ctx):
     import torch
     from paper_1111_6091_gb300 import cpmg

@@ -183,3 +183,23 @@ def test_graph_replay_matches_eager(cpmg_ctx):
     assert r0["iters_setup"] == r1["iters_setup"] and r0["iters_solve"] == r1["iters_solve"]
     for a, b in zip(A0 + B0, A1 + B1):
         assert np.array_equal(a, b)
+
+
+def test_restriction_on_tensor_cores_keeps_the_fixed_point(cpmg_ctx):
+    """The coarse tensors only shape the FAS corrections (Algorithm 2), so the multilevel solve
+    with the split-BF16 tensor-core restriction reaches the same factors as with the FP32
+    CUDA-core restriction, and both match the oracle's solution."""
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((64, 40, 36), 3, congruence=0.5, eta_homo=0.001, dtype=np.float32, seed=5)
+    ref = MG.multilevel(p.Z.astype(np.float64), p.A0, p.tfms, MG.Options(coarsest=(8, 8, 8), tol=1e-9))
+    got = []
+    for tc in (0, 1):
+        A = dev(cpmg, p.A0)
+        tf = [dev(cpmg, b) for b in p.tfms]
+        r = cpmg.cpmg_decompose(cpmg_ctx, cpmg.colmajor(p.Z), A, tf, precision=cpmg.PREC_MIXED, tol=1e-9,
+                                coarsest=(8, 8, 8), als_fallback=1, ttm_tensor_cores=tc)
+        assert r["status"] == cpmg.OK and r["g"] < 1e-9
+        got.append(host(cpmg, A))
+    assert align.factor_error(got[0], got[1]) <= 1e-6
+    if ref.converged:
+        assert align.factor_error(ref.A, got[1]) <= 1e-6
