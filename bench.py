@@ -225,6 +225,12 @@ def run_gpu(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_step = float(t.item())
 
+    if args.solve_only:
+        if rank == 0:
+            print(json.dumps({"solve_only": True, "ms": ms, "launches": int(launches)}), flush=True)
+        ctx.close()
+        return
+
     # end to end through the C ABI with pinned host buffers
     Zh = cpmg.colmajor(p.Z, device="cpu", pin=True)
     Ah = [cpmg.colmajor(a, device="cpu", pin=True) for a in p.A0]
@@ -270,6 +276,9 @@ def run_gpu(args):
         ctx.profile(False)
     gbs4 = b4 / (ms4 * 1e-3 / n4) / 1e9
     ttm4 = ttm_400cubed(ctx, stream, Z4, hbm, how)
+    del Z4, A4
+    batched = run_batched(ctx, stream, args.batch_count) if args.batch_count > 0 else None
+    served = run_served(args.serve_requests) if args.serve_requests > 0 else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -297,6 +306,8 @@ def run_gpu(args):
         "mttkrp_400cubed_fp32": {"achieved": gbs4, "peak": hbm, "unit": "GB/s", "frac": gbs4 / hbm,
                                  "avg_us": ms4 * 1e3 / n4, "launches": n4, "peak_source": how},
         "ttm_400cubed_tc": ttm4,
+        "batched": batched,
+        "served": served,
         "cpu_baseline": cpu,
         "gpu_launches": int(launches),
         "gpu_launches_note": "kernel launches per step issued by libcpmg (graph replays count their kernels)",
@@ -361,6 +372,125 @@ def peaks_tensor():
         return 1900.0  # fallback burst figure
 
 
+BATCH_COUNT, BATCH_TOL, BATCH_MAX_IT, BATCH_CHECK = 512, 1e-8, 1000, 8
+
+
+def batch_problems(count, seed=0):
+    """The uneven batch workload (synth.batch_specs): 1% noise, float32, no test blocks."""
+    from paper_1111_6091_gb300 import synth
+    return [synth.make_problem(sp["dims"], sp["R"], congruence=sp["congruence"], eta_homo=0.01,
+                               dtype=np.float32, seed=sp["seed"], n_t=0)
+            for sp in synth.batch_specs(count, seed)]
+
+
+def run_batched(ctx, stream, count=BATCH_COUNT):
+    """Batched CP-ALS of `count` uneven tensors to g < 1e-8 (at most 1000 sweeps each) in MIXED
+    and in FP64 arithmetic, and the same MIXED solves as a loop of per-tensor cp_als_sweep calls."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    probs = batch_problems(count)
+    with torch.cuda.stream(stream):
+        Zs = [cpmg.colmajor(p.Z) for p in probs]
+        A0 = [[cpmg.colmajor(a) for a in p.A0] for p in probs]
+        As = [[a.clone() for a in A] for A in A0]
+    torch.cuda.synchronize()
+
+    def reset():
+        with torch.cuda.stream(stream):
+            for A, B in zip(As, A0):
+                for a, b in zip(A, B):
+                    a.copy_(b)
+        torch.cuda.synchronize()
+
+    out = {"count": count, "tol": BATCH_TOL, "max_sweeps": BATCH_MAX_IT, "check_every": BATCH_CHECK}
+    zbytes = [p.Z.nbytes for p in probs]
+    for name, prec in (("mixed", cpmg.PREC_MIXED), ("fp64", cpmg.PREC_FP64)):
+        reset()
+        # first call tunes the unit sizes for these shape classes; time the second
+        cpmg.cpmg_batch_solve(ctx, Zs, As, precision=prec, tol=BATCH_TOL, max_als_iters=BATCH_MAX_IT,
+                              check_every=BATCH_CHECK)
+        reset()
+        t0 = time.perf_counter()
+        st, res = cpmg.cpmg_batch_solve(ctx, Zs, As, precision=prec, tol=BATCH_TOL, max_als_iters=BATCH_MAX_IT,
+                                        check_every=BATCH_CHECK)
+        dt = time.perf_counter() - t0
+        sweeps = sum(r["iters_als"] for r in res)
+        zsw = sum(r["iters_als"] * len(p.Z.shape) * b for r, p, b in zip(res, probs, zbytes))
+        out[name] = {"seconds": dt, "converged": sum(r["status"] == cpmg.OK for r in res),
+                     "tensor_sweeps": sweeps, "tensor_sweeps_per_s": sweeps / dt,
+                     "sweep_z_gbs": zsw / dt / 1e9}
+    # per-tensor launch loop (the same MIXED solves one tensor at a time)
+    reset()
+    t0 = time.perf_counter()
+    conv = 0
+    with torch.cuda.stream(stream):
+        for Z, A in zip(Zs, As):
+            r = cpmg.cp_als_sweep(ctx, Z, A, BATCH_MAX_IT, precision=cpmg.PREC_MIXED, tol=BATCH_TOL,
+                                  check_every=BATCH_CHECK)
+            conv += r["status"] == cpmg.OK
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out["per_tensor_loop_mixed"] = {"seconds": dt, "converged": conv}
+    out["speedup_vs_loop"] = dt / out["mixed"]["seconds"]
+    out["mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
+SERVE_RATE, SERVE_LARGE_FRAC = 2000.0, 0.05
+
+
+def run_served(nreq, pool_small=96, pool_large=4, seed=12345):
+    """Poisson arrivals (2000 requests/s) of CP-ALS requests to g < 1e-8 (at most 1000 sweeps):
+    95% drawn from a pool of tensors of the batch workload, 5% 256^3 R=8 tensors; admission
+    budget 120 GB.  Served with MIXED and with plain FP64 arithmetic; p50/p99 latency and
+    throughput of each."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg, synth
+    small = batch_problems(pool_small, seed=1)
+    rng = np.random.default_rng(seed)
+    large = [synth.make_problem((256, 256, 256), 8, congruence=float(rng.uniform(0.5, 0.95)), eta_homo=0.01,
+                                dtype=np.float32, seed=1000 + k, n_t=0) for k in range(pool_large)]
+    arrivals = np.cumsum(rng.exponential(1.0 / SERVE_RATE, nreq))
+    picks = [("L", int(rng.integers(0, pool_large))) if rng.random() < SERVE_LARGE_FRAC
+             else ("S", int(rng.integers(0, pool_small))) for _ in range(nreq)]
+    out = {"requests": nreq, "rate_per_s": SERVE_RATE, "large_fraction": SERVE_LARGE_FRAC, "tol": BATCH_TOL,
+           "max_sweeps": BATCH_MAX_IT, "budget_gb": 120}
+    for name, prec in (("mixed", cpmg.PREC_MIXED), ("fp64", cpmg.PREC_FP64)):
+        stream = torch.cuda.Stream()
+        ctx = cpmg.Context(0, stream=stream.cuda_stream)
+        srv = cpmg.Server(ctx, budget_bytes=120 * 10**9, sweeps_per_launch=BATCH_CHECK)
+        Zd = {("S", k): cpmg.colmajor(p.Z) for k, p in enumerate(small)}
+        Zd.update({("L", k): cpmg.colmajor(p.Z) for k, p in enumerate(large)})
+        A0 = {key: [cpmg.colmajor(a) for a in (small if key[0] == "S" else large)[key[1]].A0] for key in Zd}
+        As = [[a.clone() for a in A0[key]] for key in picks]
+        torch.cuda.synchronize()
+        # warm: one request per shape class, so the unit-size tuning is not in the timed run
+        warm = [srv.submit(Zd[key], [a.clone() for a in A0[key]], precision=prec, tol=BATCH_TOL,
+                           max_als_iters=BATCH_MAX_IT) for key in Zd]
+        torch.cuda.synchronize()
+        srv.wait(600.0)
+        for t in warm:
+            srv.poll(t)
+        t0 = time.perf_counter()
+        tickets = []
+        for i, key in enumerate(picks):
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            tickets.append(srv.submit(Zd[key], As[i], precision=prec, tol=BATCH_TOL, max_als_iters=BATCH_MAX_IT))
+        srv.wait(900.0)
+        dt = time.perf_counter() - t0
+        lats, conv = [], 0
+        for t in tickets:
+            r = srv.poll(t)
+            lats.append(r["seconds"])
+            conv += r["status"] == cpmg.OK
+        lats = np.sort(np.array(lats))
+        out[name] = {"p50_s": float(np.percentile(lats, 50)), "p99_s": float(np.percentile(lats, 99)),
+                     "req_per_s": nreq / dt, "seconds": dt, "converged": conv}
+        ctx.close()
+    return out
+
+
 def run_ttm_case(args):
     """Small case for profiler captures: one level-0 restriction of the 400^3 float tensor on
     tensor cores (three k_ttm_tc launches)."""
@@ -401,6 +531,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-only", action="store_true", help="profiler case: the timed solves only")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT, help="batched workload size (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the served workload (20000 for the full stream; 0: skip)")
     args = ap.parse_args()
     if args.impl != "reference":
         from paper_1111_6091_gb300 import build

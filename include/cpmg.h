@@ -221,6 +221,55 @@ int cpmg_hier_level_info(const cpmg_hier* hier, int level, int64_t* dims, int* c
 int cpmg_decompose(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A,
                    double* const* A_test, const cpmg_opts* opts, cpmg_result* result);
 
+/* ---- batched form -------------------------------------------------------------------- */
+
+/* CP-ALS (Section 3: for n = 1..N, A^(n) <- Z_(n) Phi^(n) (Gamma^(n))^+, then Eq. ALSnorm;
+ * components sorted by decreasing lambda at the end) on `count` independent tensors at once,
+ * each stopping when its g of Eq. gradConv drops below opts->tol or after opts->max_als_iters
+ * sweeps.  Z[t]: device tensor, order 2..4, float32 or float64; R[t] in 1..8; A[t]: Z[t].N
+ * device float64 I_n x R column-major factor arrays (initial guess in, result out), owned by
+ * the caller and not aliased between tensors.  opts: precision (FP32 / DF / MIXED / FP64, as
+ * for cp_als_sweep), tol, max_als_iters, mixed_switch; check_every > 0 = sweeps between
+ * g evaluations (default 8 when <= 0; the last evaluation may come up to check_every - 1 sweeps
+ * after g first fell below tol).  All sweeps of all tensors run in one cooperative persistent
+ * kernel per check interval; each tensor's arithmetic does not depend on the rest of the batch,
+ * so a tensor's factors are bitwise the same alone and in any batch.  The unit size is chosen by
+ * timing candidates on the first call for a batch size class (cached in the context).
+ * results[t] gets f (from the Gram identity 1/2(||Z||^2 - 2<M, A> + sum Hadamard of Grams),
+ * float64), g, iters_als and status.  Returns CPMG_OK when every tensor converged, else the
+ * first non-OK status among them (or the call's own error). */
+int cpmg_batch_solve(cpmg_ctx* ctx, int count, const cpmg_tensor* Z, const int* R, double* const* const* A,
+                     const cpmg_opts* opts, cpmg_result* results);
+
+/* ---- served form ---------------------------------------------------------------------- */
+/* A request server with continuous batching on the context.  Submitted CP-ALS problems (the
+ * same problem statement as cpmg_batch_solve) queue in arrival order; a worker thread admits
+ * them into the running batch while the HBM they hold (tensor, factors, MTTKRP partials and
+ * Grams) fits the server's budget and fewer than max_active run; it runs sweeps_per_launch
+ * sweeps of every running request per launch of the batched kernel, evaluates g, and retires
+ * finished requests between launches, so requests join and leave while others are on the GPU.
+ * A request's arithmetic does not depend on the other requests (same unit sizes, same sweep
+ * counts between checks), so its result is bitwise the same alone and in the mix.
+ * Once serving, the context accepts only server calls (other solver calls are not thread-safe
+ * with the worker).  Z and A must stay valid until the request is polled as done. */
+
+/* hbm_budget_bytes: admission cap (0 = none); max_active (<= 0: keep, default 1024);
+ * sweeps_per_launch (<= 0: keep, default 8); unit_elements: fixed MTTKRP unit size for every
+ * request (0: autotuned per shape class and cached in the context). */
+int cpmg_server_config(cpmg_ctx* ctx, size_t hbm_budget_bytes, int max_active, int sweeps_per_launch,
+                       int64_t unit_elements);
+/* Queue a request; *ticket identifies it.  CPMG_OUT_OF_BUDGET if it alone exceeds the budget. */
+int cpmg_server_submit(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A, const cpmg_opts* opts,
+                       uint64_t* ticket);
+/* CPMG_PENDING while queued or running; CPMG_OK once done, with *result (seconds = latency
+ * from submission); the ticket is then released.  CPMG_INVALID_ARG for an unknown ticket. */
+int cpmg_server_poll(cpmg_ctx* ctx, uint64_t ticket, cpmg_result* result);
+/* Block until no request is queued or running (CPMG_PENDING after timeout_s seconds). */
+int cpmg_server_wait(cpmg_ctx* ctx, double timeout_s);
+/* Latency percentiles (submission to completion) and throughput (completions per second since
+ * the first submission) over every completed request. */
+int cpmg_server_stats(cpmg_ctx* ctx, double* p50_s, double* p99_s, double* req_per_s, int64_t* completed);
+
 /* Per-kernel timing: when enabled, each launch of the finest-level MTTKRP main kernel is
  * bracketed by CUDA events on the context's stream; the statistics accumulate until reset.
  * kind: 0 = FP32 launches, 1 = float64-accurate (pairs of floats), 2 = FP64.  bytes_per_launch

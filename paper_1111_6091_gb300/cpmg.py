@@ -89,6 +89,15 @@ _SIGS = {
                                     C.POINTER(C.c_double)]),
     "cpmg_profile_reset": (C.c_int, [_P]),
     "cpmg_launch_count": (C.c_int64, [_P]),
+    "cpmg_batch_solve": (C.c_int, [_P, C.c_int, C.POINTER(cpmg_tensor), C.POINTER(C.c_int), _PP,
+                                   C.POINTER(cpmg_opts), C.POINTER(cpmg_result)]),
+    "cpmg_server_config": (C.c_int, [_P, C.c_size_t, C.c_int, C.c_int, C.c_int64]),
+    "cpmg_server_submit": (C.c_int, [_P, C.POINTER(cpmg_tensor), C.c_int, _PP, C.POINTER(cpmg_opts),
+                                     C.POINTER(C.c_uint64)]),
+    "cpmg_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(cpmg_result)]),
+    "cpmg_server_wait": (C.c_int, [_P, C.c_double]),
+    "cpmg_server_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int64)]),
 }
 
 
@@ -251,6 +260,66 @@ def cpmg_ttm(ctx, Z, Rhat, tensor_cores=0):
     Y = torch.empty(tuple(reversed(out_dims)), dtype=Z.dtype, device=Z.device)
     _check(lib().cpmg_ttm(ctx.h, C.byref(d), ptrs, ic, int(tensor_cores), C.c_void_p(Y.data_ptr())), "cpmg_ttm")
     return Y
+
+
+def cpmg_batch_solve(ctx, Zs, As, opts=None, **kw):
+    """Batched CP-ALS on the device tensors ``Zs`` with factor lists ``As`` (updated in place).
+    Returns (status, list of result dicts)."""
+    o = opts or make_opts(**kw)
+    n = len(Zs)
+    descs = (cpmg_tensor * n)()
+    ranks = (C.c_int * n)()
+    keep = []
+    rows = (C.c_void_p * n)()
+    for t, (Z, A) in enumerate(zip(Zs, As)):
+        descs[t] = tensor_desc(Z)
+        ranks[t] = A[0].shape[0]
+        p = _ptrs(A)
+        keep.append(p)
+        rows[t] = C.cast(p, C.c_void_p)
+    res = (cpmg_result * n)()
+    s = lib().cpmg_batch_solve(ctx.h, n, descs, ranks, C.cast(rows, _PP), C.byref(o), res)
+    _check(s, "cpmg_batch_solve", allow=(OK, NOT_CONVERGED, NUMERIC))
+    return s, [result_dict(r) for r in res]
+
+
+class Server:
+    """Request server on a context (continuous batching of CP-ALS problems)."""
+
+    def __init__(self, ctx, budget_bytes=0, max_active=0, sweeps_per_launch=0, unit_elements=0):
+        self.ctx = ctx
+        self._keep = {}
+        _check(lib().cpmg_server_config(ctx.h, int(budget_bytes), int(max_active), int(sweeps_per_launch),
+                                        int(unit_elements)), "cpmg_server_config")
+
+    def submit(self, Z, A, opts=None, **kw):
+        o = opts or make_opts(**kw)
+        d = tensor_desc(Z)
+        p = _ptrs(A)
+        t = C.c_uint64()
+        _check(lib().cpmg_server_submit(self.ctx.h, C.byref(d), A[0].shape[0], p, C.byref(o), C.byref(t)),
+               "cpmg_server_submit")
+        self._keep[t.value] = (Z, A, p)
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else the result dict."""
+        r = cpmg_result()
+        s = lib().cpmg_server_poll(self.ctx.h, C.c_uint64(ticket), C.byref(r))
+        if s == PENDING:
+            return None
+        _check(s, "cpmg_server_poll")
+        self._keep.pop(ticket, None)
+        return result_dict(r)
+
+    def wait(self, timeout_s=600.0):
+        return lib().cpmg_server_wait(self.ctx.h, float(timeout_s))
+
+    def stats(self):
+        p50, p99, rps, n = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
+        _check(lib().cpmg_server_stats(self.ctx.h, C.byref(p50), C.byref(p99), C.byref(rps), C.byref(n)),
+               "cpmg_server_stats")
+        return {"p50_s": p50.value, "p99_s": p99.value, "req_per_s": rps.value, "completed": n.value}
 
 
 def cpmg_eval_fg(ctx, Z, A):

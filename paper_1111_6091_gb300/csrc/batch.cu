@@ -1,0 +1,1277 @@
+// Batched CP-ALS: the relaxation sweep of Section 3 (A^(n) <- Z_(n) Phi^(n) (Gamma^(n))^+ for
+// n = 1..N, then Eq. ALSnorm) on many independent, unevenly sized tensors at once, with the
+// stopping test of Eq. gradConv per tensor.
+//
+// One cooperative, persistent kernel runs k whole sweeps of every active tensor followed by one
+// g evaluation.  Inside it, phases are separated by a grid barrier (bounded wait):
+//   units(n)   warps walk the list of MTTKRP work units of mode n of all tensors; a unit is
+//              (tensor, block of 64 rows of the first mode, chunk of columns) and writes float64
+//              partial sums to a slot of its own, so each tensor's arithmetic is independent of
+//              what else is in the batch
+//   finish(n)  one block per tensor: ordered reduction of the partials into M^(n), the R x R
+//              solve with Gamma^(n) = Hadamard of the other Grams (Cholesky, or the eigen
+//              pseudoinverse when it fails), the Gram of the new A^(n)
+//   normalize  Eq. ALSnorm per tensor, with the column norms from the Gram diagonals
+//   eval       MTTKRPs of all modes in float64-accurate arithmetic, ||A Gamma - M||^2 per mode,
+//              g, the stopping and precision-switch decisions, all on the device
+// Unit sizes (elements per unit) come from a small autotuner that times candidate lists on the
+// batch itself.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ctx.cuh"
+#include "linalg.cuh"
+
+namespace cpmg {
+
+constexpr int kBR = 8;          // largest rank of the batched kernels (columns padded to 8)
+constexpr int kBModes = 4;      // largest order
+constexpr int kBRows = 64;      // first-mode rows per unit (two per lane)
+constexpr int kBThreads = 256;
+constexpr int kBWarps = kBThreads / 32;
+constexpr int kGramStride = kBR * kBR;
+
+enum { BP_FP32 = 0, BP_FP64 = 1, BP_DF = 3 };
+enum { BS_RUNNING = -1 };
+
+// One problem of the batch (device copy; the kernel updates the state fields).
+struct BTen {
+  const void* Z;
+  double* A[kBModes];
+  double* gram;                 // kBModes x 8 x 8
+  double* part[kBModes];        // partial sums of the MTTKRP of each mode
+  int64_t dims[kBModes];
+  int nk[kBModes];              // partial slots per output row (mode > 0) or column chunks (mode 0)
+  int N, R, zf64;
+  int prec, gprec;              // sweep / evaluation arithmetic
+  int policy;                   // cpmg_precision of the request
+  int active;
+  int init;                     // 1: ||Z||^2 and the Grams still to be computed
+  int status;
+  int iters, max_iters;
+  int stall;
+  double znorm2;
+  double tol, mixed_switch;
+  double g, g_best, f;
+  double res2[kBModes], m2[kBModes], zin;
+};
+
+struct BUnit {
+  int t, mode, rb, k;
+  int64_t c0, c1;               // column range (mode 0) or range of the columns sharing i_n
+  int64_t in_idx;               // i_n (mode > 0)
+};
+
+struct BArgs {
+  BTen* ten;
+  int nten;
+  const BUnit* units[kBModes];
+  int64_t nunits[kBModes];
+  int maxN;
+  int nsweeps;
+  int eval;                     // 1: evaluate g and decide; 2: MTTKRP phases only (autotuner)
+  unsigned* bar;                // [0] arrivals, [1] generation
+  int* err;
+  int* nactive;
+};
+
+// ------------------------------------------------------------------ arithmetic per precision
+template <int P> struct BT;
+template <> struct BT<BP_FP32> { using V = float; };
+template <> struct BT<BP_FP64> { using V = double; };
+template <> struct BT<BP_DF> { using V = df; };
+
+template <typename V> __device__ __forceinline__ V bconv(double x);
+template <> __device__ __forceinline__ float bconv<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ double bconv<double>(double x) { return x; }
+template <> __device__ __forceinline__ df bconv<df>(double x) { return df_from_double(x); }
+
+template <typename V> __device__ __forceinline__ V bzero();
+template <> __device__ __forceinline__ float bzero<float>() { return 0.f; }
+template <> __device__ __forceinline__ double bzero<double>() { return 0.0; }
+template <> __device__ __forceinline__ df bzero<df>() { return {0.f, 0.f}; }
+
+__device__ __forceinline__ void bfma(float& acc, float z, float w) { acc = __fmaf_rn(z, w, acc); }
+__device__ __forceinline__ void bfma(double& acc, float z, double w) { acc = __fma_rn((double)z, w, acc); }
+__device__ __forceinline__ void bfma(double& acc, double z, double w) { acc = __fma_rn(z, w, acc); }
+__device__ __forceinline__ void bfma(df& acc, float z, df w) { acc = df_add(acc, df_mul_f(z, w)); }
+
+__device__ __forceinline__ double bto_d(float x) { return (double)x; }
+__device__ __forceinline__ double bto_d(double x) { return x; }
+__device__ __forceinline__ double bto_d(df x) { return df_to_double(x); }
+
+// a * y in the compute precision, returned as float64 (the cross-lane sums run in float64)
+__device__ __forceinline__ double bmul_d(double a, float y) { return (double)((float)a * y); }
+__device__ __forceinline__ double bmul_d(double a, double y) { return a * y; }
+__device__ __forceinline__ double bmul_d(double a, df y) { return df_to_double(df_mul(df_from_double(a), y)); }
+
+// ------------------------------------------------------------------ grid barrier (bounded)
+__device__ __forceinline__ uint64_t bclock() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_sync(unsigned* bar, int* err) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = bclock();
+      while (*gen == g) {
+        if (bclock() - t0 > 2000000000ull) {
+          atomicOr(err, 2);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// ------------------------------------------------------------------ MTTKRP unit (one warp)
+template <int P, typename TZ>
+__device__ void unit_run(const BTen& T, const BUnit& u, int lane, void* wsv, int64_t* wc) {
+  using V = typename BT<P>::V;
+  V* ws = reinterpret_cast<V*>(wsv);
+  const int N = T.N, R = T.R, n = u.mode;
+  const int64_t I0 = T.dims[0];
+  const TZ* Z = reinterpret_cast<const TZ*>(T.Z);
+  int64_t Lp = 1;
+  for (int m = 1; m < n; ++m) Lp *= T.dims[m];
+  const int64_t In = T.dims[n];
+  const int64_t r0 = (int64_t)u.rb * kBRows;
+  const int64_t rend = (r0 + kBRows < I0) ? r0 + kBRows : I0;
+  V acc[2][kBR];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) acc[q][r] = bzero<V>();
+  for (int64_t jb = u.c0; jb < u.c1; jb += 32) {
+    const int cnt = (int)(u.c1 - jb < 32 ? u.c1 - jb : 32);
+    if (lane < cnt) {
+      const int64_t j = jb + lane;
+      const int64_t col = (n == 0) ? j : (j % Lp) + Lp * (u.in_idx + In * (j / Lp));
+      wc[lane] = col;
+      double w[kBR];
+#pragma unroll
+      for (int r = 0; r < kBR; ++r) w[r] = 1.0;
+      int64_t rem = col;
+      for (int m = 1; m < N; ++m) {
+        const int64_t Im = T.dims[m];
+        const int64_t im = rem % Im;
+        rem /= Im;
+        if (m != n) {
+          const double* Am = T.A[m];
+#pragma unroll
+          for (int r = 0; r < kBR; ++r)
+            if (r < R) w[r] *= Am[im + Im * r];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kBR; ++r) ws[lane * kBR + r] = (r < R) ? bconv<V>(w[r]) : bzero<V>();
+    }
+    __syncwarp();
+    for (int jj = 0; jj < cnt; ++jj) {
+      const int64_t col = wc[jj];
+      V wr[kBR];
+#pragma unroll
+      for (int r = 0; r < kBR; ++r) wr[r] = ws[jj * kBR + r];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int64_t i1 = r0 + lane + 32 * q;
+        if (i1 < rend) {
+          const TZ z = Z[i1 + I0 * col];
+#pragma unroll
+          for (int r = 0; r < kBR; ++r) bfma(acc[q][r], z, wr[r]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (n == 0) {
+    double* Pp = T.part[0] + ((int64_t)u.k * I0) * kBR;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int64_t i1 = r0 + lane + 32 * q;
+      if (i1 < rend)
+#pragma unroll
+        for (int r = 0; r < kBR; ++r) Pp[i1 * kBR + r] = bto_d(acc[q][r]);
+    }
+  } else {
+    const double* A0 = T.A[0];
+    double t[kBR];
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int64_t i1 = r0 + lane + 32 * q;
+        if (i1 < rend && r < R) s += bmul_d(A0[i1 + I0 * r], acc[q][r]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      t[r] = s;
+    }
+    if (lane == 0) {
+      double* Pp = T.part[n] + ((int64_t)u.in_idx * T.nk[n] + u.k) * kBR;
+#pragma unroll
+      for (int r = 0; r < kBR; ++r) Pp[r] = t[r];
+    }
+  }
+}
+
+struct BSmem {
+  double ws[kBWarps][32 * kBR];   // Khatri-Rao rows of 32 columns (float / double / df)
+  int64_t wc[kBWarps][32];
+  double G[kBR * kBR], L[kBR * kBR], Pi[kBR * kBR], V[kBR * kBR], w[kBR];
+  double red[3][kBThreads];
+  double sc[kBModes][kBR];
+  int chol_ok;
+};
+
+__device__ void phase_units(const BArgs& a, int n, bool eval, BSmem& sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kBWarps + warp, nw = (int64_t)gridDim.x * kBWarps;
+  for (int64_t ui = gw; ui < a.nunits[n]; ui += nw) {
+    const BUnit u = a.units[n][ui];
+    const BTen& T = a.ten[u.t];
+    if (!T.active) continue;
+    const int p = eval ? T.gprec : T.prec;
+    if (T.zf64) unit_run<BP_FP64, double>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+    else if (p == BP_FP32) unit_run<BP_FP32, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+    else if (p == BP_DF) unit_run<BP_DF, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+    else unit_run<BP_FP64, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+  }
+}
+
+// M^(n) row i from the partials, in a fixed order
+__device__ __forceinline__ void row_sum(const BTen& T, int n, int64_t i, double* m) {
+#pragma unroll
+  for (int r = 0; r < kBR; ++r) m[r] = 0.0;
+  if (n == 0) {
+    const int64_t I0 = T.dims[0];
+    for (int k = 0; k < T.nk[0]; ++k) {
+      const double* p = T.part[0] + ((int64_t)k * I0 + i) * kBR;
+#pragma unroll
+      for (int r = 0; r < kBR; ++r) m[r] += p[r];
+    }
+  } else {
+    const double* p = T.part[n] + (i * T.nk[n]) * kBR;
+    for (int k = 0; k < T.nk[n]; ++k)
+#pragma unroll
+      for (int r = 0; r < kBR; ++r) m[r] += p[(int64_t)k * kBR + r];
+  }
+}
+
+// deterministic block sum of one value per thread (thread 0 adds in thread order)
+__device__ double bblock_sum(double v, double* buf) {
+  buf[threadIdx.x] = v;
+  __syncthreads();
+  __shared__ double tot;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) s += buf[k];
+    tot = s;
+  }
+  __syncthreads();
+  const double r = tot;
+  __syncthreads();
+  return r;
+}
+
+// update: the ALS update of mode n and its Gram.  !update: ||A Gamma - M||^2, ||M||^2 (and
+// <M, A> for the last mode) at the current factors.
+__device__ void finish_tensor(BTen& T, int n, bool update, BSmem& sm) {
+  const int R = T.R, N = T.N, tid = threadIdx.x;
+  const int64_t In = T.dims[n];
+  double* A = T.A[n];
+  for (int e = tid; e < R * R; e += blockDim.x) {
+    double v = 1.0;
+    for (int m = 0; m < N; ++m)
+      if (m != n) v *= T.gram[m * kGramStride + (e / R) * kBR + (e % R)];
+    sm.G[e] = v;
+  }
+  __syncthreads();
+  if (update && tid == 0) {
+    double dmax = 0.0;
+    for (int i = 0; i < R; ++i) dmax = fmax(dmax, sm.G[i * R + i]);
+    const double eps = 2.220446049250313e-16;
+    const double thresh = R * eps * (dmax > 0 ? dmax : 1.0);
+    int ok = 1;
+    for (int i = 0; i < R * R; ++i) sm.L[i] = 0.0;
+    for (int j = 0; j < R && ok; ++j) {
+      double s = sm.G[j * R + j];
+      for (int k = 0; k < j; ++k) s -= sm.L[j * R + k] * sm.L[j * R + k];
+      if (!(s > thresh)) {
+        ok = 0;
+        break;
+      }
+      sm.L[j * R + j] = sqrt(s);
+      for (int i = j + 1; i < R; ++i) {
+        double t = sm.G[i * R + j];
+        for (int k = 0; k < j; ++k) t -= sm.L[i * R + k] * sm.L[j * R + k];
+        sm.L[i * R + j] = t / sm.L[j * R + j];
+      }
+    }
+    sm.chol_ok = ok;
+    if (!ok) {
+      double Gc[kBR * kBR];
+      for (int i = 0; i < R * R; ++i) Gc[i] = sm.G[i];
+      jacobi_eig_dev(Gc, sm.V, sm.w, R);
+      double wmax = 0.0;
+      for (int i = 0; i < R; ++i) wmax = fmax(wmax, fabs(sm.w[i]));
+      const double cut = R * eps * wmax;
+      for (int i = 0; i < R; ++i)
+        for (int j = 0; j < R; ++j) {
+          double s = 0.0;
+          for (int k = 0; k < R; ++k)
+            if (fabs(sm.w[k]) > cut) s += sm.V[i * R + k] * sm.V[j * R + k] / sm.w[k];
+          sm.Pi[i * R + j] = s;
+        }
+    }
+  }
+  __syncthreads();
+  double res = 0.0, m2 = 0.0, zin = 0.0;
+  for (int64_t i = tid; i < In; i += blockDim.x) {
+    double m[kBR];
+    row_sum(T, n, i, m);
+    if (update) {
+      double x[kBR];
+      if (sm.chol_ok) {
+        for (int r = 0; r < R; ++r) {
+          double t = m[r];
+          for (int k = 0; k < r; ++k) t -= sm.L[r * R + k] * x[k];
+          x[r] = t / sm.L[r * R + r];
+        }
+        for (int r = R - 1; r >= 0; --r) {
+          double t = x[r];
+          for (int k = r + 1; k < R; ++k) t -= sm.L[k * R + r] * x[k];
+          x[r] = t / sm.L[r * R + r];
+        }
+      } else {
+        for (int r = 0; r < R; ++r) {
+          double t = 0.0;
+          for (int k = 0; k < R; ++k) t += m[k] * sm.Pi[k * R + r];
+          x[r] = t;
+        }
+      }
+      for (int r = 0; r < R; ++r) A[i + In * r] = x[r];
+    } else {
+      for (int r = 0; r < R; ++r) {
+        double ag = 0.0;
+        for (int k = 0; k < R; ++k) ag += A[i + In * k] * sm.G[k * R + r];
+        const double d = ag - m[r];
+        res += d * d;
+        m2 += m[r] * m[r];
+        zin += m[r] * A[i + In * r];
+      }
+    }
+  }
+  __syncthreads();
+  if (update) {
+    const int npairs = R * (R + 1) / 2;
+    for (int p = tid; p < npairs; p += blockDim.x) {
+      int r = 0, q = p;
+      while (q >= R - r) {
+        q -= R - r;
+        ++r;
+      }
+      const int c = r + q;
+      double acc = 0.0;
+      for (int64_t i = 0; i < In; ++i) acc = __fma_rn(A[i + In * r], A[i + In * c], acc);
+      T.gram[n * kGramStride + r * kBR + c] = acc;
+      T.gram[n * kGramStride + c * kBR + r] = acc;
+    }
+  } else {
+    const double s_res = bblock_sum(res, sm.red[0]);
+    const double s_m2 = bblock_sum(m2, sm.red[1]);
+    const double s_zin = bblock_sum(zin, sm.red[2]);
+    if (tid == 0) {
+      T.res2[n] = s_res;
+      T.m2[n] = s_m2;
+      if (n == N - 1) T.zin = s_zin;
+    }
+  }
+  __syncthreads();
+}
+
+// Eq. ALSnorm with the column norms taken from the Gram diagonals
+__device__ void normalize_tensor(BTen& T, BSmem& sm) {
+  const int R = T.R, N = T.N, tid = threadIdx.x;
+  if (tid < R) {
+    double nr[kBModes], prod = 1.0;
+    for (int m = 0; m < N; ++m) {
+      nr[m] = sqrt(T.gram[m * kGramStride + tid * kBR + tid]);
+      prod *= nr[m];
+    }
+    const double lam = pow(prod, 1.0 / N);
+    for (int m = 0; m < N; ++m) sm.sc[m][tid] = nr[m] > 0 ? lam / nr[m] : 1.0;
+  }
+  __syncthreads();
+  for (int m = 0; m < N; ++m) {
+    const int64_t Im = T.dims[m];
+    for (int64_t e = tid; e < Im * R; e += blockDim.x) T.A[m][e] *= sm.sc[m][e / Im];
+    for (int e = tid; e < R * R; e += blockDim.x) {
+      const int r = e / R, c = e % R;
+      T.gram[m * kGramStride + r * kBR + c] *= sm.sc[m][r] * sm.sc[m][c];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    T.iters += 1;
+    if (T.iters >= T.max_iters && T.max_iters > 0) {
+      // the last sweep is still followed by the g evaluation of this launch (if any)
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void check_tensor(BTen& T, int* nactive) {
+  double g2 = 0.0, m2 = 0.0;
+  for (int n = 0; n < T.N; ++n) {
+    g2 += T.res2[n];
+    m2 += T.m2[n];
+  }
+  const double zn = sqrt(T.znorm2);
+  const double g = sqrt(g2) / zn;
+  double cross = 0.0;
+  for (int r = 0; r < T.R; ++r)
+    for (int c = 0; c < T.R; ++c) {
+      double p = 1.0;
+      for (int n = 0; n < T.N; ++n) p *= T.gram[n * kGramStride + r * kBR + c];
+      cross += p;
+    }
+  T.f = 0.5 * (T.znorm2 - 2.0 * T.zin + cross);
+  T.g = g;
+  if (!isfinite(g)) {
+    T.status = CPMG_NUMERIC;
+    T.active = 0;
+  } else if (g < T.tol) {
+    T.status = CPMG_OK;
+    T.active = 0;
+  } else if (T.max_iters > 0 && T.iters >= T.max_iters) {
+    T.status = CPMG_NOT_CONVERGED;
+    T.active = 0;
+  } else if (T.policy == CPMG_PREC_MIXED && T.prec == BP_FP32) {
+    // float sweeps stop helping once g nears their rounding floor, or stop improving
+    const double floor_g = T.mixed_switch * 5.960464477539063e-08 * sqrt(m2) / zn;
+    if (T.g_best < 0 || g < T.g_best) {
+      T.g_best = g;
+      T.stall = 0;
+    } else {
+      T.stall += 1;
+    }
+    if (g < floor_g || T.stall >= 20) T.prec = BP_DF;
+  }
+  if (T.active) atomicAdd(nactive, 1);
+}
+
+__global__ void __launch_bounds__(kBThreads) k_batch(BArgs a) {
+  __shared__ BSmem sm;
+  bool ok = true;
+  for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
+    for (int n = 0; n < a.maxN && ok; ++n) {
+      phase_units(a, n, false, sm);
+      ok = grid_sync(a.bar, a.err);
+      for (int t = blockIdx.x; t < a.nten && ok; t += gridDim.x)
+        if (a.ten[t].active && n < a.ten[t].N) finish_tensor(a.ten[t], n, true, sm);
+      ok = ok && grid_sync(a.bar, a.err);
+    }
+    for (int t = blockIdx.x; t < a.nten && ok; t += gridDim.x)
+      if (a.ten[t].active) normalize_tensor(a.ten[t], sm);
+    ok = ok && grid_sync(a.bar, a.err);
+  }
+  if (a.eval && ok) {
+    for (int n = 0; n < a.maxN; ++n) phase_units(a, n, a.eval == 1, sm);
+    ok = grid_sync(a.bar, a.err);
+    if (a.eval == 1) {
+      for (int t = blockIdx.x; t < a.nten && ok; t += gridDim.x) {
+        if (!a.ten[t].active) continue;
+        for (int n = 0; n < a.ten[t].N; ++n) finish_tensor(a.ten[t], n, false, sm);
+        if (threadIdx.x == 0) check_tensor(a.ten[t], a.nactive);
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ setup / final kernels
+// ||Z||^2 and the Grams of every tensor (block per tensor, fixed order)
+__global__ void __launch_bounds__(kBThreads) k_batch_init(BTen* ten, int nten) {
+  __shared__ double buf[kBThreads];
+  for (int t = blockIdx.x; t < nten; t += gridDim.x) {
+    BTen& T = ten[t];
+    if (!T.init) continue;
+    int64_t P = 1;
+    for (int m = 0; m < T.N; ++m) P *= T.dims[m];
+    double s = 0.0;
+    for (int64_t e = threadIdx.x; e < P; e += blockDim.x) {
+      const double z = T.zf64 ? reinterpret_cast<const double*>(T.Z)[e] : (double)reinterpret_cast<const float*>(T.Z)[e];
+      s += z * z;
+    }
+    const double zz = bblock_sum(s, buf);
+    const int R = T.R, npairs = R * (R + 1) / 2;
+    for (int m = 0; m < T.N; ++m) {
+      const int64_t Im = T.dims[m];
+      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        int r = 0, q = p;
+        while (q >= R - r) {
+          q -= R - r;
+          ++r;
+        }
+        const int c = r + q;
+        double acc = 0.0;
+        for (int64_t i = 0; i < Im; ++i) acc = __fma_rn(T.A[m][i + Im * r], T.A[m][i + Im * c], acc);
+        T.gram[m * kGramStride + r * kBR + c] = acc;
+        T.gram[m * kGramStride + c * kBR + r] = acc;
+      }
+    }
+    if (threadIdx.x == 0) {
+      T.znorm2 = zz;
+      T.init = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// sort the rank-one terms by decreasing lambda (ties keep their order), end of Section 3
+__global__ void __launch_bounds__(kBThreads) k_batch_sort(BTen* ten, const int* idx, int count) {
+  __shared__ int perm[kBR];
+  __shared__ double tmp[kBThreads];
+  for (int q = blockIdx.x; q < count; q += gridDim.x) {
+    BTen& T = ten[idx[q]];
+    const int R = T.R, N = T.N;
+    if (threadIdx.x == 0) {
+      double lam[kBR];
+      for (int r = 0; r < R; ++r) {
+        double p = 1.0;
+        for (int m = 0; m < N; ++m) {
+          const int64_t Im = T.dims[m];
+          double s = 0.0;
+          for (int64_t i = 0; i < Im; ++i) s += T.A[m][i + Im * r] * T.A[m][i + Im * r];
+          p *= sqrt(s);
+        }
+        lam[r] = pow(p, 1.0 / N);
+        perm[r] = r;
+      }
+      for (int i = 1; i < R; ++i) {  // stable insertion sort, decreasing
+        const int pi = perm[i];
+        int j = i - 1;
+        while (j >= 0 && lam[perm[j]] < lam[pi]) {
+          perm[j + 1] = perm[j];
+          --j;
+        }
+        perm[j + 1] = pi;
+      }
+    }
+    __syncthreads();
+    for (int m = 0; m < N; ++m) {
+      const int64_t Im = T.dims[m];
+      for (int64_t i0 = 0; i0 < Im; i0 += blockDim.x / kBR) {
+        const int64_t i = i0 + threadIdx.x / kBR;
+        const int r = threadIdx.x % kBR;
+        double v = 0.0;
+        if (i < Im && r < R) v = T.A[m][i + Im * perm[r]];
+        tmp[threadIdx.x] = v;
+        __syncthreads();
+        if (i < Im && r < R) T.A[m][i + Im * r] = tmp[threadIdx.x];
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct BItem {                   // one problem as given by the caller
+  const void* Z;
+  int zf64, N, R;
+  int64_t dims[kBModes];
+  double* A[kBModes];            // device float64 factors, updated in place
+  double* gram;                  // device kBModes x 8 x 8, owned by the batch or the request
+  cpmg_opts o;
+  int64_t target;                // elements per MTTKRP unit (autotuned per shape class)
+  bool has_state;
+  BTen state;                    // device state carried over when the batch is rebuilt
+};
+
+static int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static int64_t numel_of(const BItem& it) {
+  int64_t P = 1;
+  for (int m = 0; m < it.N; ++m) P *= it.dims[m];
+  return P;
+}
+
+// Unit lists and partial-sum layout (per tensor and mode) for the items' unit sizes.
+static void plan_units(const std::vector<BItem>& items, std::vector<BUnit>* units, int* nk, size_t* part_off,
+                       size_t* part_total) {
+  for (int n = 0; n < kBModes; ++n) units[n].clear();
+  size_t off = 0;
+  for (size_t t = 0; t < items.size(); ++t) {
+    const BItem& it = items[t];
+    const int64_t I0 = it.dims[0];
+    const int64_t P = numel_of(it);
+    const int nrb = (int)cdiv64(I0, kBRows);
+    const int64_t C = std::max<int64_t>(32, cdiv64(cdiv64(it.target, std::min<int64_t>(I0, kBRows)), 32) * 32);
+    for (int n = 0; n < kBModes; ++n) {
+      part_off[t * kBModes + n] = off;
+      nk[t * kBModes + n] = 0;
+      if (n >= it.N) continue;
+      if (n == 0) {
+        const int64_t ncol = P / I0;
+        const int nch = (int)cdiv64(ncol, C);
+        nk[t * kBModes + n] = nch;
+        for (int ch = 0; ch < nch; ++ch)
+          for (int rb = 0; rb < nrb; ++rb)
+            units[0].push_back({(int)t, 0, rb, ch, ch * C, std::min<int64_t>(ncol, (ch + 1) * C), -1});
+        off += (size_t)nch * I0 * kBR;
+      } else {
+        const int64_t In = it.dims[n];
+        const int64_t ncol = P / (I0 * In);
+        const int nch = (int)cdiv64(ncol, C);
+        nk[t * kBModes + n] = nch * nrb;
+        for (int64_t i = 0; i < In; ++i)
+          for (int ch = 0; ch < nch; ++ch)
+            for (int rb = 0; rb < nrb; ++rb)
+              units[n].push_back({(int)t, n, rb, ch * nrb + rb, ch * C, std::min<int64_t>(ncol, (ch + 1) * C), i});
+        off += (size_t)In * nch * nrb * kBR;
+      }
+    }
+  }
+  *part_total = off;
+}
+
+static size_t partial_doubles_of(const BItem& it) {
+  std::vector<BItem> one(1, it);
+  std::vector<BUnit> u[kBModes];
+  int nk[kBModes];
+  size_t po[kBModes], tot = 0;
+  plan_units(one, u, nk, po, &tot);
+  return tot;
+}
+
+static BTen make_desc(const BItem& it) {
+  BTen T;
+  std::memset(&T, 0, sizeof(T));
+  if (it.has_state) T = it.state;
+  T.Z = it.Z;
+  for (int m = 0; m < kBModes; ++m) {
+    T.A[m] = it.A[m];
+    T.dims[m] = it.dims[m];
+    T.part[m] = nullptr;
+  }
+  T.gram = it.gram;
+  T.N = it.N;
+  T.R = it.R;
+  T.zf64 = it.zf64;
+  if (it.has_state) return T;
+  T.policy = it.o.precision;
+  if (it.zf64 || it.o.precision == CPMG_PREC_FP64) {
+    T.prec = BP_FP64;
+    T.gprec = BP_FP64;
+  } else {
+    T.prec = (it.o.precision == CPMG_PREC_DF) ? BP_DF : BP_FP32;
+    T.gprec = BP_DF;
+  }
+  T.active = 1;
+  T.init = 1;
+  T.status = BS_RUNNING;
+  T.max_iters = it.o.max_als_iters;
+  T.tol = it.o.tol;
+  T.mixed_switch = it.o.mixed_switch > 0 ? it.o.mixed_switch : 64.0;
+  T.g = -1.0;
+  T.g_best = -1.0;
+  return T;
+}
+
+// Device resources of one batch; buffers grow by capacity so a server can rebuild cheaply.
+struct BatchDev {
+  cpmg_ctx* c = nullptr;
+  int nten = 0, maxN = 0, grid = 0;
+  BTen* d_ten = nullptr;
+  size_t cap_ten = 0;
+  BUnit* d_units[kBModes] = {nullptr, nullptr, nullptr, nullptr};
+  size_t cap_units[kBModes] = {0, 0, 0, 0};
+  int64_t nunits[kBModes] = {0, 0, 0, 0};
+  double* d_part = nullptr;
+  size_t cap_part = 0;
+  int* d_idx = nullptr;
+  size_t cap_idx = 0;
+  unsigned* d_bar = nullptr;
+  int* d_flags = nullptr;        // [0] error, [1] active count
+  int* h_flags = nullptr;        // pinned mirror
+  std::vector<BTen> host;
+  ~BatchDev() { release(); }
+  void release() {
+    if (!c) return;
+    for (int n = 0; n < kBModes; ++n) ctx_free(c, d_units[n]), d_units[n] = nullptr, cap_units[n] = 0;
+    ctx_free(c, d_ten);
+    ctx_free(c, d_part);
+    ctx_free(c, d_idx);
+    ctx_free(c, d_bar);
+    ctx_free(c, d_flags);
+    if (h_flags) cudaFreeHost(h_flags);
+    d_ten = nullptr;
+    d_part = nullptr;
+    d_idx = nullptr;
+    d_bar = nullptr;
+    d_flags = h_flags = nullptr;
+    cap_ten = cap_part = cap_idx = 0;
+    c = nullptr;
+  }
+};
+
+template <typename T>
+static int grow(cpmg_ctx* c, T** p, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return CPMG_OK;
+  ctx_free(c, *p);
+  *p = nullptr;
+  *cap = 0;
+  const size_t n = std::max<size_t>(need, 1) + need / 4;
+  CPMG_TRY(ctx_alloc(c, reinterpret_cast<void**>(p), n * sizeof(T)));
+  *cap = n;
+  return CPMG_OK;
+}
+
+static int batch_open(cpmg_ctx* c, BatchDev& B) {
+  B.c = c;
+  CPMG_TRY(ctx_alloc(c, reinterpret_cast<void**>(&B.d_bar), 2 * sizeof(unsigned)));
+  CPMG_TRY(ctx_alloc(c, reinterpret_cast<void**>(&B.d_flags), 4 * sizeof(int)));
+  CPMG_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&B.h_flags), 4 * sizeof(int)));
+  CPMG_CUDA_TRY(cudaMemsetAsync(B.d_flags, 0, 4 * sizeof(int), ctx_stream(c)));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBThreads, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  cudaGetLastError();
+  B.grid = per_sm * ctx_sms(c);
+  return CPMG_OK;
+}
+
+// Descriptors, unit lists and partial layout for `items`; runs the init kernel for new ones.
+static int batch_load(BatchDev& B, const std::vector<BItem>& items) {
+  cudaStream_t st = ctx_stream(B.c);
+  B.nten = (int)items.size();
+  B.maxN = 0;
+  for (auto& it : items) B.maxN = std::max(B.maxN, it.N);
+  std::vector<BUnit> units[kBModes];
+  std::vector<int> nk(items.size() * kBModes, 0);
+  std::vector<size_t> poff(items.size() * kBModes, 0);
+  size_t ptotal = 0;
+  plan_units(items, units, nk.data(), poff.data(), &ptotal);
+  CPMG_TRY(grow(B.c, &B.d_part, &B.cap_part, ptotal));
+  CPMG_TRY(grow(B.c, &B.d_ten, &B.cap_ten, items.size()));
+  for (int n = 0; n < kBModes; ++n) {
+    B.nunits[n] = (int64_t)units[n].size();
+    if (units[n].empty()) continue;
+    CPMG_TRY(grow(B.c, &B.d_units[n], &B.cap_units[n], units[n].size()));
+    CPMG_CUDA_TRY(cudaMemcpyAsync(B.d_units[n], units[n].data(), units[n].size() * sizeof(BUnit),
+                                  cudaMemcpyHostToDevice, st));
+  }
+  B.host.resize(items.size());
+  bool any_init = false;
+  for (size_t t = 0; t < items.size(); ++t) {
+    B.host[t] = make_desc(items[t]);
+    for (int n = 0; n < kBModes; ++n) {
+      B.host[t].nk[n] = nk[t * kBModes + n];
+      B.host[t].part[n] = n < items[t].N ? B.d_part + poff[t * kBModes + n] : nullptr;
+    }
+    any_init = any_init || B.host[t].init;
+  }
+  CPMG_CUDA_TRY(cudaMemcpyAsync(B.d_ten, B.host.data(), B.host.size() * sizeof(BTen), cudaMemcpyHostToDevice, st));
+  if (any_init) {
+    k_batch_init<<<std::max(1, std::min(B.nten, 4 * ctx_sms(B.c))), kBThreads, 0, st>>>(B.d_ten, B.nten);
+    CPMG_CUDA_TRY(cudaGetLastError());
+    ctx_add_launches(B.c, 1);
+    CPMG_CUDA_TRY(cudaMemcpyAsync(B.host.data(), B.d_ten, B.host.size() * sizeof(BTen), cudaMemcpyDeviceToHost, st));
+  }
+  CPMG_CUDA_TRY(cudaStreamSynchronize(st));
+  return CPMG_OK;
+}
+
+static int launch_batch(BatchDev& B, int nsweeps, int eval) {
+  cudaStream_t st = ctx_stream(B.c);
+  BArgs a;
+  a.ten = B.d_ten;
+  a.nten = B.nten;
+  for (int n = 0; n < kBModes; ++n) {
+    a.units[n] = B.d_units[n];
+    a.nunits[n] = B.nunits[n];
+  }
+  a.maxN = B.maxN;
+  a.nsweeps = nsweeps;
+  a.eval = eval;
+  a.bar = B.d_bar;
+  a.err = B.d_flags;
+  a.nactive = B.d_flags + 1;
+  void* args[] = {&a};
+  CPMG_CUDA_TRY(cudaMemsetAsync(B.d_flags + 1, 0, sizeof(int), st));
+  CPMG_CUDA_TRY(cudaMemsetAsync(B.d_bar, 0, 2 * sizeof(unsigned), st));
+  CPMG_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_batch, dim3(B.grid), dim3(kBThreads), args, 0, st));
+  ctx_add_launches(B.c, 1);
+  return CPMG_OK;
+}
+
+// k sweeps + one evaluation; refreshes the host mirror of every descriptor.
+static int batch_step(BatchDev& B, int k, int* nactive) {
+  cudaStream_t st = ctx_stream(B.c);
+  CPMG_TRY(launch_batch(B, k, 1));
+  CPMG_CUDA_TRY(cudaMemcpyAsync(B.h_flags, B.d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPMG_CUDA_TRY(cudaMemcpyAsync(B.host.data(), B.d_ten, B.host.size() * sizeof(BTen), cudaMemcpyDeviceToHost, st));
+  CPMG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (B.h_flags[0]) return CPMG_TIMEOUT;
+  *nactive = B.h_flags[1];
+  return CPMG_OK;
+}
+
+static int batch_sort(BatchDev& B, const std::vector<int>& idx) {
+  if (idx.empty()) return CPMG_OK;
+  cudaStream_t st = ctx_stream(B.c);
+  CPMG_TRY(grow(B.c, &B.d_idx, &B.cap_idx, idx.size()));
+  CPMG_CUDA_TRY(cudaMemcpyAsync(B.d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  k_batch_sort<<<std::max(1, std::min((int)idx.size(), 4 * ctx_sms(B.c))), kBThreads, 0, st>>>(B.d_ten, B.d_idx,
+                                                                                             (int)idx.size());
+  CPMG_CUDA_TRY(cudaGetLastError());
+  ctx_add_launches(B.c, 1);
+  CPMG_CUDA_TRY(cudaStreamSynchronize(st));
+  return CPMG_OK;
+}
+
+// ------------------------------------------------------------------ autotuner and server state
+struct BatchState {
+  std::map<std::string, int64_t> tuned;   // unit size per shape class
+  int64_t fixed_target = 0;                // > 0: every class uses this unit size
+  // request server
+  struct Req {
+    uint64_t id;
+    BItem item;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    cpmg_result res;
+    int state;     // 0 queued, 1 running, 2 done
+    size_t bytes;  // HBM held while running (tensor, factors, partials, Gram)
+  };
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Req*> queue;
+  std::vector<Req*> active;
+  std::map<uint64_t, Req*> reqs;
+  std::vector<double> lat;
+  std::thread worker;
+  bool stop = false, started = false;
+  int worker_status = CPMG_OK;
+  uint64_t next_id = 1;
+  size_t budget = 0, reserved = 0;
+  int max_active = 1024;
+  int sweeps_per_launch = 8;
+  std::chrono::steady_clock::time_point t_first, t_last;
+  bool any = false;
+  int64_t completed = 0;
+  int64_t launches = 0;
+};
+
+static BatchState* state_of(cpmg_ctx* c) {
+  BatchState*& s = ctx_batch_state(c);
+  if (!s) s = new BatchState();
+  return s;
+}
+
+static std::string class_key(const BItem& it) {
+  const int64_t P = numel_of(it);
+  int lp = 0, li = 0;
+  while ((int64_t(1) << lp) < P) ++lp;
+  while ((int64_t(1) << li) < it.dims[0]) ++li;
+  const int prec = it.zf64 ? 9 : it.o.precision;
+  char b[64];
+  snprintf(b, sizeof(b), "N%d_R%d_p%d_i%d_P%d", it.N, it.R, prec, li, lp);
+  return b;
+}
+
+// Sets items[].target from the per-context cache; classes not seen yet are tuned jointly by
+// timing one MTTKRP pass of every mode (sweep arithmetic, no state change) per candidate.
+static int autotune(BatchDev& B, std::vector<BItem>& items) {
+  BatchState* S = state_of(B.c);
+  std::vector<int> todo;
+  for (size_t t = 0; t < items.size(); ++t) {
+    if (S->fixed_target > 0) {
+      items[t].target = S->fixed_target;
+      continue;
+    }
+    auto f = S->tuned.find(class_key(items[t]));
+    if (f != S->tuned.end()) items[t].target = f->second;
+    else todo.push_back((int)t);
+  }
+  if (todo.empty()) return CPMG_OK;
+  const int64_t cands[] = {2048, 4096, 8192, 16384, 32768};
+  cudaStream_t st = ctx_stream(B.c);
+  cudaEvent_t e0, e1;
+  CPMG_CUDA_TRY(cudaEventCreate(&e0));
+  CPMG_CUDA_TRY(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int64_t best = 8192;
+  int rc = CPMG_OK;
+  for (int64_t cand : cands) {
+    for (int t : todo) items[t].target = cand;
+    if ((rc = batch_load(B, items)) != CPMG_OK) break;
+    if ((rc = launch_batch(B, 0, 2)) != CPMG_OK) break;  // warm
+    cudaEventRecord(e0, st);
+    if ((rc = launch_batch(B, 0, 2)) != CPMG_OK) break;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = CPMG_CUDA_ERROR;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cand;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CPMG_TRY(rc);
+  for (int t : todo) {
+    items[t].target = best;
+    S->tuned[class_key(items[t])] = best;
+  }
+  // descriptors were loaded with init done: keep the computed ||Z||^2 and Grams
+  for (size_t t = 0; t < items.size(); ++t) {
+    items[t].has_state = true;
+    items[t].state = B.host[t];
+  }
+  return CPMG_OK;
+}
+
+static int check_item(const cpmg_tensor* Z, int R, double* const* A, const cpmg_opts* o, BItem* it) {
+  if (!Z || !A || !o) return CPMG_INVALID_ARG;
+  if (Z->N < 2 || Z->N > kBModes || R < 1 || R > kBR || !Z->data) return CPMG_INVALID_ARG;
+  if (Z->mem != CPMG_MEM_DEVICE || (Z->dtype != CPMG_F32 && Z->dtype != CPMG_F64)) return CPMG_INVALID_ARG;
+  if (o->precision < 0 || o->precision > 3) return CPMG_INVALID_ARG;
+  int64_t P = 1;
+  for (int m = 0; m < Z->N; ++m) {
+    if (Z->dims[m] < 1 || !A[m]) return CPMG_INVALID_ARG;
+    P *= Z->dims[m];
+  }
+  if (P >= (int64_t(1) << 40)) return CPMG_INVALID_ARG;
+  std::memset(it, 0, sizeof(*it));
+  it->Z = Z->data;
+  it->zf64 = Z->dtype == CPMG_F64;
+  it->N = Z->N;
+  it->R = R;
+  for (int m = 0; m < kBModes; ++m) {
+    it->dims[m] = m < Z->N ? Z->dims[m] : 1;
+    it->A[m] = m < Z->N ? A[m] : nullptr;
+  }
+  it->o = *o;
+  it->target = 8192;
+  it->has_state = false;
+  return CPMG_OK;
+}
+
+static void fill_result(const BTen& T, cpmg_result* r, double seconds) {
+  std::memset(r, 0, sizeof(*r));
+  r->f = T.f;
+  r->g = T.g;
+  r->iters_als = T.iters;
+  r->levels = 1;
+  r->status = T.status == BS_RUNNING ? CPMG_NOT_CONVERGED : T.status;
+  r->seconds = seconds;
+}
+
+static double now_sec() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------------ server worker
+static void server_loop(cpmg_ctx* c, BatchState* S) {
+  cudaSetDevice(ctx_device(c));
+  BatchDev B;
+  int rc = batch_open(c, B);
+  bool dirty = true;
+  std::vector<BItem> items;
+  while (rc == CPMG_OK) {
+    std::vector<BatchState::Req*> admitted;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      while (!S->stop && S->queue.empty() && S->active.empty()) S->cv.wait_for(lk, std::chrono::milliseconds(5));
+      if (S->stop) break;
+      // admission by HBM budget, in arrival order
+      while (!S->queue.empty() && (int)S->active.size() < S->max_active) {
+        BatchState::Req* q = S->queue.front();
+        if (S->budget && S->reserved + q->bytes > S->budget && !S->active.empty()) break;
+        S->queue.pop_front();
+        S->active.push_back(q);
+        S->reserved += q->bytes;
+        q->state = 1;
+        admitted.push_back(q);
+        dirty = true;
+      }
+    }
+    for (auto* q : admitted)
+      if (!q->item.gram) {
+        void* g = nullptr;
+        if ((rc = ctx_alloc(c, &g, kBModes * kGramStride * sizeof(double))) != CPMG_OK) break;
+        q->item.gram = reinterpret_cast<double*>(g);
+      }
+    if (rc != CPMG_OK) break;
+    if (dirty) {
+      items.clear();
+      for (auto* q : S->active) items.push_back(q->item);
+      if ((rc = autotune(B, items)) != CPMG_OK) break;
+      if ((rc = batch_load(B, items)) != CPMG_OK) break;
+      for (size_t t = 0; t < items.size(); ++t) {
+        S->active[t]->item.target = items[t].target;
+        S->active[t]->item.has_state = true;
+        S->active[t]->item.state = B.host[t];
+      }
+      dirty = false;
+    }
+    int nact = 0;
+    if ((rc = batch_step(B, S->sweeps_per_launch, &nact)) != CPMG_OK) break;
+    S->launches += 1;
+    std::vector<int> fin;
+    for (size_t t = 0; t < S->active.size(); ++t) {
+      S->active[t]->item.state = B.host[t];
+      if (!B.host[t].active) fin.push_back((int)t);
+    }
+    if (!fin.empty()) {
+      if ((rc = batch_sort(B, fin)) != CPMG_OK) break;
+      const auto now = std::chrono::steady_clock::now();
+      std::lock_guard<std::mutex> lk(S->mu);
+      std::vector<BatchState::Req*> keep;
+      size_t fi = 0;
+      for (size_t t = 0; t < S->active.size(); ++t) {
+        BatchState::Req* q = S->active[t];
+        if (fi < fin.size() && fin[fi] == (int)t) {
+          ++fi;
+          q->t_done = now;
+          const double lat = std::chrono::duration<double>(now - q->t_submit).count();
+          fill_result(B.host[t], &q->res, lat);
+          q->state = 2;
+          S->reserved -= q->bytes;
+          S->lat.push_back(lat);
+          S->completed += 1;
+          S->t_last = now;
+          ctx_free(c, q->item.gram);
+          q->item.gram = nullptr;
+        } else {
+          keep.push_back(q);
+        }
+      }
+      S->active.swap(keep);
+      dirty = true;
+      S->cv.notify_all();
+    }
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->worker_status = rc;
+  // fail everything still pending so pollers do not wait forever
+  for (auto* q : S->active) {
+    std::memset(&q->res, 0, sizeof(q->res));
+    q->res.status = rc == CPMG_OK ? CPMG_CANCELLED : rc;
+    q->state = 2;
+    ctx_free(c, q->item.gram);
+    q->item.gram = nullptr;
+  }
+  S->active.clear();
+  for (auto* q : S->queue) {
+    std::memset(&q->res, 0, sizeof(q->res));
+    q->res.status = rc == CPMG_OK ? CPMG_CANCELLED : rc;
+    q->state = 2;
+  }
+  S->queue.clear();
+  S->reserved = 0;
+  S->cv.notify_all();
+}
+
+void batch_state_destroy(cpmg_ctx* c) {
+  BatchState*& s = ctx_batch_state(c);
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto& kv : s->reqs) delete kv.second;
+  delete s;
+  s = nullptr;
+}
+
+}  // namespace cpmg
+
+using namespace cpmg;
+
+extern "C" {
+
+int cpmg_batch_solve(cpmg_ctx* c, int count, const cpmg_tensor* Z, const int* R, double* const* const* A,
+                     const cpmg_opts* opts, cpmg_result* results) {
+  cudaGetLastError();
+  if (!c || count < 1 || !Z || !R || !A || !opts || !results) return CPMG_INVALID_ARG;
+  {
+    BatchState* S = state_of(c);
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->started) return CPMG_INVALID_ARG;  // the context serves requests
+  }
+  const double t0 = now_sec();
+  std::vector<BItem> items(count);
+  for (int t = 0; t < count; ++t) CPMG_TRY(check_item(&Z[t], R[t], A[t], opts, &items[t]));
+  BatchDev B;
+  double* grams = nullptr;
+  int st = batch_open(c, B);
+  if (st == CPMG_OK)
+    st = ctx_alloc(c, reinterpret_cast<void**>(&grams), (size_t)count * kBModes * kGramStride * sizeof(double));
+  if (st == CPMG_OK) {
+    for (int t = 0; t < count; ++t) items[t].gram = grams + (size_t)t * kBModes * kGramStride;
+    st = autotune(B, items);
+  }
+  if (st == CPMG_OK) st = batch_load(B, items);
+  const int k = opts->check_every > 0 ? opts->check_every : 8;
+  if (st == CPMG_OK) {
+    const int64_t maxl = (std::max(opts->max_als_iters, 1) + k - 1) / k + 2;
+    int nact = count;
+    for (int64_t l = 0; l < maxl && nact > 0 && st == CPMG_OK; ++l) st = batch_step(B, k, &nact);
+  }
+  if (st == CPMG_OK) {
+    std::vector<int> all(count);
+    for (int t = 0; t < count; ++t) all[t] = t;
+    st = batch_sort(B, all);
+  }
+  const double dt = now_sec() - t0;
+  int worst = st;
+  for (int t = 0; t < count; ++t) {
+    if (st == CPMG_OK) {
+      fill_result(B.host[t], &results[t], dt);
+      if (results[t].status != CPMG_OK && worst == CPMG_OK) worst = results[t].status;
+    } else {
+      std::memset(&results[t], 0, sizeof(cpmg_result));
+      results[t].status = st;
+    }
+  }
+  ctx_free(c, grams);
+  return worst;
+}
+
+int cpmg_server_config(cpmg_ctx* c, size_t hbm_budget_bytes, int max_active, int sweeps_per_launch,
+                       int64_t unit_elements) {
+  if (!c || max_active < 0 || sweeps_per_launch < 0 || unit_elements < 0) return CPMG_INVALID_ARG;
+  BatchState* S = state_of(c);
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->budget = hbm_budget_bytes;
+  if (max_active > 0) S->max_active = max_active;
+  if (sweeps_per_launch > 0) S->sweeps_per_launch = sweeps_per_launch;
+  S->fixed_target = unit_elements;
+  return CPMG_OK;
+}
+
+int cpmg_server_submit(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A, const cpmg_opts* opts,
+                       uint64_t* ticket) {
+  if (!c || !ticket) return CPMG_INVALID_ARG;
+  BItem it;
+  CPMG_TRY(check_item(Z, R, A, opts, &it));
+  BatchState* S = state_of(c);
+  auto* q = new BatchState::Req();
+  q->item = it;
+  q->item.gram = nullptr;
+  q->state = 0;
+  q->t_submit = std::chrono::steady_clock::now();
+  const int64_t P = numel_of(it);
+  size_t fb = 0;
+  for (int m = 0; m < it.N; ++m) fb += (size_t)it.dims[m] * R * 8;
+  q->bytes = (size_t)P * (it.zf64 ? 8 : 4) + fb + partial_doubles_of(it) * 8 + kBModes * kGramStride * 8;
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->budget && q->bytes > S->budget) {
+    delete q;
+    return CPMG_OUT_OF_BUDGET;
+  }
+  if (S->worker_status != CPMG_OK) {
+    delete q;
+    return S->worker_status;
+  }
+  q->id = S->next_id++;
+  S->reqs[q->id] = q;
+  S->queue.push_back(q);
+  if (!S->any) {
+    S->any = true;
+    S->t_first = q->t_submit;
+  }
+  if (!S->started) {
+    S->started = true;
+    S->worker = std::thread(server_loop, c, S);
+  }
+  *ticket = q->id;
+  lk.unlock();
+  S->cv.notify_all();
+  return CPMG_OK;
+}
+
+int cpmg_server_poll(cpmg_ctx* c, uint64_t ticket, cpmg_result* out) {
+  if (!c || !out) return CPMG_INVALID_ARG;
+  BatchState* S = state_of(c);
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto f = S->reqs.find(ticket);
+  if (f == S->reqs.end()) return CPMG_INVALID_ARG;
+  BatchState::Req* q = f->second;
+  if (q->state != 2) return CPMG_PENDING;
+  *out = q->res;
+  S->reqs.erase(f);
+  delete q;
+  return CPMG_OK;
+}
+
+int cpmg_server_wait(cpmg_ctx* c, double timeout_s) {
+  if (!c) return CPMG_INVALID_ARG;
+  BatchState* S = state_of(c);
+  std::unique_lock<std::mutex> lk(S->mu);
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+  while (!S->queue.empty() || !S->active.empty()) {
+    if (S->cv.wait_until(lk, deadline) == std::cv_status::timeout) return CPMG_PENDING;
+  }
+  return S->worker_status;
+}
+
+int cpmg_server_stats(cpmg_ctx* c, double* p50_s, double* p99_s, double* req_per_s, int64_t* completed) {
+  if (!c) return CPMG_INVALID_ARG;
+  BatchState* S = state_of(c);
+  std::lock_guard<std::mutex> lk(S->mu);
+  std::vector<double> v = S->lat;
+  std::sort(v.begin(), v.end());
+  auto pct = [&](double p) {
+    if (v.empty()) return 0.0;
+    const size_t i = (size_t)std::min<double>((double)v.size() - 1, std::ceil(p * v.size()) - 1);
+    return v[i];
+  };
+  if (p50_s) *p50_s = pct(0.50);
+  if (p99_s) *p99_s = pct(0.99);
+  if (req_per_s) {
+    const double span = S->completed ? std::chrono::duration<double>(S->t_last - S->t_first).count() : 0.0;
+    *req_per_s = span > 0 ? S->completed / span : 0.0;
+  }
+  if (completed) *completed = S->completed;
+  return CPMG_OK;
+}
+
+}  // extern "C"

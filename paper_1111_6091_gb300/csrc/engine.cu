@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "ctx.cuh"
 #include "dense.cuh"
 #include "fused.cuh"
 #include "mttkrp.cuh"
@@ -58,6 +59,7 @@ struct cpmg_ctx {
   int64_t launches = 0;
   const void* prof_Z = nullptr;  // tensor whose MTTKRPs are profiled (the finest level)
   bool capturing = false;        // a CUDA graph capture is open on `stream`
+  cpmg::BatchState* batch = nullptr;  // batched solver / request server (batch.cu)
 };
 
 namespace cpmg {
@@ -92,6 +94,18 @@ static void dfree(cpmg_ctx* c, void* p) {
   }
   cudaFree(p);
 }
+
+namespace cpmg {
+int ctx_alloc(cpmg_ctx* c, void** p, size_t bytes) { return dalloc(c, p, bytes); }
+void ctx_free(cpmg_ctx* c, void* p) { dfree(c, p); }
+cudaStream_t ctx_stream(const cpmg_ctx* c) { return c->stream; }
+int ctx_device(const cpmg_ctx* c) { return c->device; }
+int ctx_sms(const cpmg_ctx* c) { return c->num_sms; }
+size_t ctx_budget(const cpmg_ctx* c) { return c->budget; }
+size_t ctx_in_use(const cpmg_ctx* c) { return c->in_use; }
+void ctx_add_launches(cpmg_ctx* c, int64_t n) { c->launches += n; }
+BatchState*& ctx_batch_state(cpmg_ctx* c) { return c->batch; }
+}  // namespace cpmg
 
 template <typename T>
 static int dalloc_t(cpmg_ctx* c, T** p, size_t count) {
@@ -993,6 +1007,7 @@ int cpmg_create(cpmg_ctx** out, int device, size_t budget, void* stream) {
 void cpmg_destroy(cpmg_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  batch_state_destroy(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto& p : c->pool) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
