@@ -302,6 +302,41 @@ __device__ double bblock_sum(double v, double* buf) {
   return r;
 }
 
+// stripe-parallel Gram of A (I x R, column-major) into gram (row stride kBR), fixed order:
+// rows are split into stripes summed in parallel, then the stripes in order (GB300's float64
+// units have long dependent latencies, so the chains stay short)
+__device__ void gram_rows(const double* A, int64_t I, int R, double* gram, double* buf) {
+  const int npairs = R * (R + 1) / 2;
+  const int stripes = (int)blockDim.x / npairs > 0 ? (int)blockDim.x / npairs : 1;
+  const int t = threadIdx.x;
+  if (t < stripes * npairs) {
+    const int p = t % npairs, sidx = t / npairs;
+    int r = 0, q = p;
+    while (q >= R - r) {
+      q -= R - r;
+      ++r;
+    }
+    const int c = r + q;
+    double acc = 0.0;
+    for (int64_t i = sidx; i < I; i += stripes) acc = __fma_rn(A[i + I * r], A[i + I * c], acc);
+    buf[t] = acc;
+  }
+  __syncthreads();
+  for (int p = t; p < npairs; p += blockDim.x) {
+    int r = 0, q = p;
+    while (q >= R - r) {
+      q -= R - r;
+      ++r;
+    }
+    const int c = r + q;
+    double acc = 0.0;
+    for (int k = 0; k < stripes; ++k) acc += buf[k * npairs + p];
+    gram[r * kBR + c] = acc;
+    gram[c * kBR + r] = acc;
+  }
+  __syncthreads();
+}
+
 // update: the ALS update of mode n and its Gram.  !update: ||A Gamma - M||^2, ||M||^2 (and
 // <M, A> for the last mode) at the current factors.
 __device__ void finish_tensor(BTen& T, int n, bool update, BSmem& sm) {
@@ -313,72 +348,49 @@ __device__ void finish_tensor(BTen& T, int n, bool update, BSmem& sm) {
     for (int m = 0; m < N; ++m)
       if (m != n) v *= T.gram[m * kGramStride + (e / R) * kBR + (e % R)];
     sm.G[e] = v;
+    sm.Pi[e] = v;
   }
   __syncthreads();
-  if (update && tid == 0) {
+  if (update) {
     double dmax = 0.0;
     for (int i = 0; i < R; ++i) dmax = fmax(dmax, sm.G[i * R + i]);
     const double eps = 2.220446049250313e-16;
     const double thresh = R * eps * (dmax > 0 ? dmax : 1.0);
-    int ok = 1;
-    for (int i = 0; i < R * R; ++i) sm.L[i] = 0.0;
-    for (int j = 0; j < R && ok; ++j) {
-      double s = sm.G[j * R + j];
-      for (int k = 0; k < j; ++k) s -= sm.L[j * R + k] * sm.L[j * R + k];
-      if (!(s > thresh)) {
-        ok = 0;
-        break;
-      }
-      sm.L[j * R + j] = sqrt(s);
-      for (int i = j + 1; i < R; ++i) {
-        double t = sm.G[i * R + j];
-        for (int k = 0; k < j; ++k) t -= sm.L[i * R + k] * sm.L[j * R + k];
-        sm.L[i * R + j] = t / sm.L[j * R + j];
+    if (!gj_inverse(sm.Pi, R, thresh, &sm.chol_ok)) {
+      // singular Gamma: the pseudoinverse from a symmetric eigendecomposition
+      if (tid == 0) {
+        double Gc[kBR * kBR];
+        for (int i = 0; i < R * R; ++i) Gc[i] = sm.G[i];
+        jacobi_eig_dev(Gc, sm.V, sm.w, R);
+        double wmax = 0.0;
+        for (int i = 0; i < R; ++i) wmax = fmax(wmax, fabs(sm.w[i]));
+        const double cut = R * eps * wmax;
+        for (int i = 0; i < R; ++i)
+          for (int j = 0; j < R; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < R; ++k)
+              if (fabs(sm.w[k]) > cut) s += sm.V[i * R + k] * sm.V[j * R + k] / sm.w[k];
+            sm.Pi[i * R + j] = s;
+          }
       }
     }
-    sm.chol_ok = ok;
-    if (!ok) {
-      double Gc[kBR * kBR];
-      for (int i = 0; i < R * R; ++i) Gc[i] = sm.G[i];
-      jacobi_eig_dev(Gc, sm.V, sm.w, R);
-      double wmax = 0.0;
-      for (int i = 0; i < R; ++i) wmax = fmax(wmax, fabs(sm.w[i]));
-      const double cut = R * eps * wmax;
-      for (int i = 0; i < R; ++i)
-        for (int j = 0; j < R; ++j) {
-          double s = 0.0;
-          for (int k = 0; k < R; ++k)
-            if (fabs(sm.w[k]) > cut) s += sm.V[i * R + k] * sm.V[j * R + k] / sm.w[k];
-          sm.Pi[i * R + j] = s;
-        }
-    }
+    __syncthreads();
   }
-  __syncthreads();
   double res = 0.0, m2 = 0.0, zin = 0.0;
   for (int64_t i = tid; i < In; i += blockDim.x) {
     double m[kBR];
     row_sum(T, n, i, m);
     if (update) {
-      double x[kBR];
-      if (sm.chol_ok) {
-        for (int r = 0; r < R; ++r) {
-          double t = m[r];
-          for (int k = 0; k < r; ++k) t -= sm.L[r * R + k] * x[k];
-          x[r] = t / sm.L[r * R + r];
-        }
-        for (int r = R - 1; r >= 0; --r) {
-          double t = x[r];
-          for (int k = r + 1; k < R; ++k) t -= sm.L[k * R + r] * x[k];
-          x[r] = t / sm.L[r * R + r];
-        }
-      } else {
-        for (int r = 0; r < R; ++r) {
-          double t = 0.0;
-          for (int k = 0; k < R; ++k) t += m[k] * sm.Pi[k * R + r];
-          x[r] = t;
+#pragma unroll
+      for (int r = 0; r < kBR; ++r) {
+        if (r < R) {
+          double x = 0.0;
+#pragma unroll
+          for (int k = 0; k < kBR; ++k)
+            if (k < R) x = __fma_rn(m[k], sm.Pi[k * R + r], x);
+          A[i + In * r] = x;
         }
       }
-      for (int r = 0; r < R; ++r) A[i + In * r] = x[r];
     } else {
       for (int r = 0; r < R; ++r) {
         double ag = 0.0;
@@ -392,19 +404,7 @@ __device__ void finish_tensor(BTen& T, int n, bool update, BSmem& sm) {
   }
   __syncthreads();
   if (update) {
-    const int npairs = R * (R + 1) / 2;
-    for (int p = tid; p < npairs; p += blockDim.x) {
-      int r = 0, q = p;
-      while (q >= R - r) {
-        q -= R - r;
-        ++r;
-      }
-      const int c = r + q;
-      double acc = 0.0;
-      for (int64_t i = 0; i < In; ++i) acc = __fma_rn(A[i + In * r], A[i + In * c], acc);
-      T.gram[n * kGramStride + r * kBR + c] = acc;
-      T.gram[n * kGramStride + c * kBR + r] = acc;
-    }
+    gram_rows(A, In, R, T.gram + n * kGramStride, sm.red[0]);
   } else {
     const double s_res = bblock_sum(res, sm.red[0]);
     const double s_m2 = bblock_sum(m2, sm.red[1]);
@@ -421,14 +421,19 @@ __device__ void finish_tensor(BTen& T, int n, bool update, BSmem& sm) {
 // Eq. ALSnorm with the column norms taken from the Gram diagonals
 __device__ void normalize_tensor(BTen& T, BSmem& sm) {
   const int R = T.R, N = T.N, tid = threadIdx.x;
+  for (int e = tid; e < N * R; e += blockDim.x) {
+    const int m = e / R, r = e % R;
+    sm.V[e] = sqrt(T.gram[m * kGramStride + r * kBR + r]);
+  }
+  __syncthreads();
   if (tid < R) {
-    double nr[kBModes], prod = 1.0;
+    double prod = 1.0;
+    for (int m = 0; m < N; ++m) prod *= sm.V[m * R + tid];
+    const double lam = nth_root(prod, N);
     for (int m = 0; m < N; ++m) {
-      nr[m] = sqrt(T.gram[m * kGramStride + tid * kBR + tid]);
-      prod *= nr[m];
+      const double nr = sm.V[m * R + tid];
+      sm.sc[m][tid] = nr > 0 ? lam / nr : 1.0;
     }
-    const double lam = pow(prod, 1.0 / N);
-    for (int m = 0; m < N; ++m) sm.sc[m][tid] = nr[m] > 0 ? lam / nr[m] : 1.0;
   }
   __syncthreads();
   for (int m = 0; m < N; ++m) {
@@ -440,16 +445,21 @@ __device__ void normalize_tensor(BTen& T, BSmem& sm) {
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    T.iters += 1;
-    if (T.iters >= T.max_iters && T.max_iters > 0) {
-      // the last sweep is still followed by the g evaluation of this launch (if any)
-    }
-  }
+  if (tid == 0) T.iters += 1;
   __syncthreads();
 }
 
-__device__ void check_tensor(BTen& T, int* nactive) {
+__device__ void check_tensor(BTen& T, int* nactive, BSmem& sm) {
+  // sum over (r, c) of prod_n Upsilon^(n)_{rc} = ||[[A]]||^2, spread over threads
+  double part = 0.0;
+  for (int e = threadIdx.x; e < T.R * T.R; e += blockDim.x) {
+    const int r = e / T.R, c = e % T.R;
+    double p = 1.0;
+    for (int n = 0; n < T.N; ++n) p *= T.gram[n * kGramStride + r * kBR + c];
+    part += p;
+  }
+  const double cross = bblock_sum(part, sm.red[0]);
+  if (threadIdx.x != 0) return;
   double g2 = 0.0, m2 = 0.0;
   for (int n = 0; n < T.N; ++n) {
     g2 += T.res2[n];
@@ -457,13 +467,6 @@ __device__ void check_tensor(BTen& T, int* nactive) {
   }
   const double zn = sqrt(T.znorm2);
   const double g = sqrt(g2) / zn;
-  double cross = 0.0;
-  for (int r = 0; r < T.R; ++r)
-    for (int c = 0; c < T.R; ++c) {
-      double p = 1.0;
-      for (int n = 0; n < T.N; ++n) p *= T.gram[n * kGramStride + r * kBR + c];
-      cross += p;
-    }
   T.f = 0.5 * (T.znorm2 - 2.0 * T.zin + cross);
   T.g = g;
   if (!isfinite(g)) {
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BArgs a) {
       for (int t = blockIdx.x; t < a.nten && ok; t += gridDim.x) {
         if (!a.ten[t].active) continue;
         for (int n = 0; n < a.ten[t].N; ++n) finish_tensor(a.ten[t], n, false, sm);
-        if (threadIdx.x == 0) check_tensor(a.ten[t], a.nactive);
+        check_tensor(a.ten[t], a.nactive, sm);
         __syncthreads();
       }
     }
@@ -533,22 +536,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch_init(BTen* ten, int nten) {
       s += z * z;
     }
     const double zz = bblock_sum(s, buf);
-    const int R = T.R, npairs = R * (R + 1) / 2;
-    for (int m = 0; m < T.N; ++m) {
-      const int64_t Im = T.dims[m];
-      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-        int r = 0, q = p;
-        while (q >= R - r) {
-          q -= R - r;
-          ++r;
-        }
-        const int c = r + q;
-        double acc = 0.0;
-        for (int64_t i = 0; i < Im; ++i) acc = __fma_rn(T.A[m][i + Im * r], T.A[m][i + Im * c], acc);
-        T.gram[m * kGramStride + r * kBR + c] = acc;
-        T.gram[m * kGramStride + c * kBR + r] = acc;
-      }
-    }
+    for (int m = 0; m < T.N; ++m) gram_rows(T.A[m], T.dims[m], T.R, T.gram + m * kGramStride, buf);
     if (threadIdx.x == 0) {
       T.znorm2 = zz;
       T.init = 0;
@@ -574,7 +562,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch_sort(BTen* ten, const int* 
           for (int64_t i = 0; i < Im; ++i) s += T.A[m][i + Im * r] * T.A[m][i + Im * r];
           p *= sqrt(s);
         }
-        lam[r] = pow(p, 1.0 / N);
+        lam[r] = nth_root(p, N);
         perm[r] = r;
       }
       for (int i = 1; i < R; ++i) {  // stable insertion sort, decreasing

@@ -22,19 +22,34 @@ __global__ void k_grams(FactorPtrArgs f, unsigned mask) {
       ++cnt;
     }
   if (m < 0) return;
+  __shared__ double part[256];
   const int R = f.R;
   const int64_t I = f.I[m];
   const double* A = f.A[m];
   double* G = f.gram + (size_t)m * R * R;
+  // each pair's rows are split into stripes summed in parallel, then the stripes in order:
+  // short dependent float64 chains (GB300's float64 FMA latency is long)
   const int npairs = R * (R + 1) / 2;
-  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+  const int stripes = (int)blockDim.x / npairs > 0 ? (int)blockDim.x / npairs : 1;
+  const int t = threadIdx.x;
+  if (t < stripes * npairs) {
+    const int p = t % npairs, sidx = t / npairs;
     int r = 0, q = p;
     while (q >= R - r) { q -= R - r; ++r; }
-    const int s = r + q;
+    const int c = r + q;
     double acc = 0.0;
-    for (int64_t i = 0; i < I; ++i) acc = __fma_rn(A[i + I * r], A[i + I * s], acc);
-    G[r * R + s] = acc;
-    G[s * R + r] = acc;
+    for (int64_t i = sidx; i < I; i += stripes) acc = __fma_rn(A[i + I * r], A[i + I * c], acc);
+    part[t] = acc;
+  }
+  __syncthreads();
+  for (int p = t; p < npairs; p += blockDim.x) {
+    int r = 0, q = p;
+    while (q >= R - r) { q -= R - r; ++r; }
+    const int c = r + q;
+    double acc = 0.0;
+    for (int k = 0; k < stripes; ++k) acc += part[k * npairs + p];
+    G[r * R + c] = acc;
+    G[c * R + r] = acc;
   }
 }
 
@@ -42,7 +57,7 @@ int launch_grams(const FactorSet& f, unsigned mask, cudaStream_t st) {
   int cnt = 0;
   for (int k = 0; k < f.N; ++k) cnt += (mask >> k) & 1u;
   if (cnt == 0) return CPMG_OK;
-  k_grams<<<cnt, 160, 0, st>>>(fargs(f), mask);
+  k_grams<<<cnt, 256, 0, st>>>(fargs(f), mask);
   CPMG_CUDA_TRY(cudaGetLastError());
   return CPMG_OK;
 }
@@ -176,13 +191,19 @@ int launch_gs_update(const FactorSet& f, int mode, const double* M, const double
 
 // ------------------------------------------------------------------ normalization
 __global__ void k_norm_scales(FactorPtrArgs f, double* scale) {
+  __shared__ double nrm[kMaxModes * kR];
   const int R = f.R;
+  for (int e = threadIdx.x; e < f.N * R; e += blockDim.x) {
+    const int m = e / R, r = e % R;
+    nrm[e] = sqrt(f.gram[(size_t)m * R * R + r * R + r]);
+  }
+  __syncthreads();
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     double prod = 1.0;
-    for (int m = 0; m < f.N; ++m) prod *= sqrt(f.gram[(size_t)m * R * R + r * R + r]);
-    const double lam = pow(prod, 1.0 / f.N);
+    for (int m = 0; m < f.N; ++m) prod *= nrm[m * R + r];
+    const double lam = nth_root(prod, f.N);
     for (int m = 0; m < f.N; ++m) {
-      const double nr = sqrt(f.gram[(size_t)m * R * R + r * R + r]);
+      const double nr = nrm[m * R + r];
       scale[m * R + r] = nr > 0 ? lam / nr : 1.0;
     }
   }
@@ -213,7 +234,7 @@ __global__ void k_apply_scales(FactorPtrArgs f, const double* scale) {
 // scale buffer: N*R doubles placed right after the Grams (the FactorSet allocator reserves it)
 int launch_normalize(const FactorSet& f, cudaStream_t st) {
   double* scale = f.gram + (size_t)f.N * f.R * f.R;
-  k_norm_scales<<<1, 32, 0, st>>>(fargs(f), scale);
+  k_norm_scales<<<1, 128, 0, st>>>(fargs(f), scale);
   CPMG_CUDA_TRY(cudaGetLastError());
   int64_t total = (int64_t)f.N * f.R * f.R;
   for (int m = 0; m < f.N; ++m) total += f.dims[m] * f.R;
@@ -227,13 +248,14 @@ __global__ void k_sort(FactorPtrArgs f, double* scratch) {
   __shared__ int perm[kR];
   __shared__ double lam[kR];
   const int R = f.R;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double prod = 1.0;
+    for (int m = 0; m < f.N; ++m) prod *= sqrt(f.gram[(size_t)m * R * R + r * R + r]);
+    lam[r] = nth_root(prod, f.N);
+    perm[r] = r;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    for (int r = 0; r < R; ++r) {
-      double prod = 1.0;
-      for (int m = 0; m < f.N; ++m) prod *= sqrt(f.gram[(size_t)m * R * R + r * R + r]);
-      lam[r] = pow(prod, 1.0 / f.N);
-      perm[r] = r;
-    }
     for (int i = 1; i < R; ++i) {  // stable insertion sort, decreasing lambda
       const int p = perm[i];
       int j = i - 1;
@@ -409,11 +431,26 @@ __global__ void k_f_direct(FArgs a) {
 }
 
 __global__ void k_f_final(const double* partial, int nb, double* out) {
+  // strided per-thread sums, then a fixed-order tree over threads
+  __shared__ double sd[256], sz[256];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    a += partial[2 * k];
+    b += partial[2 * k + 1];
+  }
+  sd[threadIdx.x] = a;
+  sz[threadIdx.x] = b;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sd[threadIdx.x] += sd[threadIdx.x + h];
+      sz[threadIdx.x] += sz[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    double sd = 0.0, sz = 0.0;
-    for (int b = 0; b < nb; ++b) { sd += partial[2 * b]; sz += partial[2 * b + 1]; }
-    out[0] = sd;
-    out[1] = sz;
+    out[0] = sd[0];
+    out[1] = sz[0];
   }
 }
 
@@ -435,7 +472,7 @@ int launch_f_direct(const Shape& s, const void* Z, int dtype, const FactorSet& f
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + 7) / 8, 1024));
   k_f_direct<<<nb, 256, 0, st>>>(a);
   CPMG_CUDA_TRY(cudaGetLastError());
-  k_f_final<<<1, 32, 0, st>>>(partial, nb, out);
+  k_f_final<<<1, 256, 0, st>>>(partial, nb, out);
   CPMG_CUDA_TRY(cudaGetLastError());
   return CPMG_OK;
 }

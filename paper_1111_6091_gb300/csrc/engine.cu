@@ -287,7 +287,7 @@ static int prof_ttm(cpmg_ctx* c, const Shape& s, int dtype, const double* const*
 // kind < 0: M = MTTKRP (reduced by the finish kernel).  kind 0 / 1: the MTTKRP followed by the
 // fused reduction + ALS solve / Gauss-Seidel (with right-hand side F) + Gram refresh of mode n.
 static int run_mttkrp_k(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, const FactorSet& f, int mode,
-                        int prec, double* M, int kind, const double* F, int gs_sweeps);
+                        int prec, double* M, int kind, const double* F, int gs_sweeps, bool normalize = false);
 
 static int run_mttkrp(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, const FactorSet& f, int mode,
                       int prec, double* M) {
@@ -295,7 +295,7 @@ static int run_mttkrp(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, con
 }
 
 static int run_mttkrp_k(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, const FactorSet& f, int mode,
-                        int prec, double* M, int kind, const double* F, int gs_sweeps) {
+                        int prec, double* M, int kind, const double* F, int gs_sweeps, bool normalize) {
   const MttkrpPlan* p = nullptr;
   CPMG_TRY(get_plan(c, s, mode, f.R, prec, dtype, Z, &p));
   CPMG_TRY(ensure_scratch(c, p->partial_bytes(), p->tables_bytes()));
@@ -312,7 +312,7 @@ static int run_mttkrp_k(cpmg_ctx* c, const Shape& s, const void* Z, int dtype, c
   c->launches += (p->use_tma || p->has_in || p->has_out) ? 3 : 2;
   if (kind >= 0)
     CPMG_TRY(launch_finish_update(*p, w, f, mode, kind, F, gs_sweeps, nullptr, c->gscratch, c->dstatus + 2,
-                                  c->dstatus, c->stream));
+                                  c->dstatus, c->stream, normalize));
   if (c->pending.size() > 512) CPMG_TRY(profile_collect(c));
   return CPMG_OK;
 }
@@ -518,10 +518,10 @@ struct Solver {
 // One ALS iteration over all modes plus normalization (Section 3, Eq. ALSnorm).
 static int als_sweep(Solver& S, const Level& L, int lvl, FactorSet& f) {
   const int prec = S.prec_for(lvl, L.dtype);
-  for (int n = 0; n < f.N; ++n) CPMG_TRY(run_mttkrp_k(S.c, L.s, L.Z, L.dtype, f, n, prec, nullptr, 0, nullptr, 0));
+  // the last mode's update also normalizes (Eq. ALSnorm) in its final block
+  for (int n = 0; n < f.N; ++n)
+    CPMG_TRY(run_mttkrp_k(S.c, L.s, L.Z, L.dtype, f, n, prec, nullptr, 0, nullptr, 0, n == f.N - 1));
   if (lvl == 0 && prec != P_FP32) S.refine_sweeps++;
-  CPMG_TRY(launch_normalize(f, S.st));
-  S.c->launches += 2;
   return CPMG_OK;
 }
 

@@ -1,13 +1,17 @@
 // One kernel for what follows an MTTKRP inside a relaxation sweep: the ordered reduction of
 // the MTTKRP partial sums into M = Z_(n) Phi^(n), the R x R solve of the ALS update
 // (A^(n) <- M Gamma^+, Section 3) or the Gauss-Seidel sweeps of BNGS (A^(n) Gamma = M + F,
-// Section 5.2), and the refresh of Upsilon^(n) = A^(n)^T A^(n) (Eq. Gamma).
+// Section 5.2), the refresh of Upsilon^(n) = A^(n)^T A^(n) (Eq. Gamma), and optionally the
+// normalization of Eq. ALSnorm that ends an ALS sweep.
 //
-// Every block factorizes Gamma^(n) (the Hadamard product of the other Grams) in shared memory,
-// then each warp handles rows of A^(n): lanes sum the partials of the row in a fixed order, a
-// shuffle tree combines them, lane 0 solves the row.  Each block then forms the Gram of its own
-// rows; the last block to finish (atomic ticket) sums the block Grams in block order.  The
-// summation orders depend only on the shapes, so results are bitwise reproducible.
+// Every block inverts Gamma^(n) (the Hadamard product of the other Grams) in shared memory with
+// R*R threads, then each warp handles rows of A^(n): lanes sum the partials of the row in a
+// fixed order, a shuffle tree combines them, and lane r forms component r of M(i,:) Gamma^+.
+// GB300's float64 units have long dependent latencies (tens of cycles per FMA, hundreds per
+// division or square root), so the kernel keeps serial float64 chains short.  Each block then
+// forms the Gram of its own rows; the last block to finish (atomic ticket) sums the block Grams
+// in block order.  The summation orders depend only on the shapes, so results are bitwise
+// reproducible.
 #include "fused.cuh"
 #include "linalg.cuh"
 
@@ -16,7 +20,7 @@
 namespace cpmg {
 
 constexpr int kR = kMaxRank;
-constexpr int kWarps = 8;
+constexpr int kMaxThreads = 256;  // R*R threads invert Gamma, so R = 16 needs 256
 
 struct FuseArgs {
   FactorPtrArgs f;
@@ -31,6 +35,7 @@ struct FuseArgs {
   double* gscratch;       // gridDim.x x R(R+1)/2
   int* ticket;
   int* status;
+  int normalize;          // 1: apply Eq. ALSnorm to the whole factor set after the update
 };
 
 __device__ __forceinline__ double part_at(const FuseArgs& a, int64_t idx) {
@@ -38,59 +43,111 @@ __device__ __forceinline__ double part_at(const FuseArgs& a, int64_t idx) {
                  : (double)reinterpret_cast<const float*>(a.partial)[idx];
 }
 
-__global__ void __launch_bounds__(kWarps * 32) k_finish_update(FuseArgs a) {
-  __shared__ double G[kR * kR], L[kR * kR], Pi[kR * kR], V[kR * kR], w[kR];
-  __shared__ int chol_ok;
+// Rarely taken or once-per-launch paths live in separate, non-inlined functions: the kernel
+// runs once per mode update with a cold instruction cache, so the hot path is kept short.
+
+// singular Gamma (thread 0): W = Gamma^+ from a symmetric eigendecomposition
+__device__ __noinline__ void pinv_fallback(const double* G, double* W, double* V, double* w, int R) {
+  const double eps = 2.220446049250313e-16;
+  double Gc[kR * kR];
+  for (int i = 0; i < R * R; ++i) Gc[i] = G[i];
+  jacobi_eig_dev(Gc, V, w, R);
+  double wmax = 0.0;
+  for (int i = 0; i < R; ++i) wmax = fmax(wmax, fabs(w[i]));
+  const double cut = R * eps * wmax;
+  for (int i = 0; i < R; ++i)
+    for (int j = 0; j < R; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < R; ++k)
+        if (fabs(w[k]) > cut) s += V[i * R + k] * V[j * R + k] / w[k];
+      W[i * R + j] = s;
+    }
+}
+
+// Gauss-Seidel sweeps of BNGS on one row: x Gamma = m + f, from the current row of A
+__device__ __noinline__ void gs_row(const double* m, const FuseArgs& a, double* A, int64_t i, int64_t I,
+                                    const double* G, const double* dinv) {
+  const int R = a.f.R;
+  double x[kR], b[kR];
+  for (int r = 0; r < R; ++r) {
+    x[r] = A[i + I * r];
+    b[r] = m[r] + (a.F ? a.F[i + I * r] : 0.0);
+  }
+  for (int it = 0; it < a.gs_sweeps; ++it)
+    for (int r = 0; r < R; ++r) {
+      double t = b[r];
+      for (int k = 0; k < R; ++k)
+        if (k != r) t -= G[r * R + k] * x[k];
+      x[r] = t * dinv[r];
+    }
+  for (int r = 0; r < R; ++r) A[i + I * r] = x[r];
+}
+
+// Eq. ALSnorm on the whole factor set (block-wide); scales also stored after the Grams
+__device__ __noinline__ void normalize_all(const FuseArgs& a, double* nrm, double* sc) {
+  const int N = a.f.N, R = a.f.R;
+  for (int e = threadIdx.x; e < N * R; e += blockDim.x) {
+    const int m = e / R, r = e % R;
+    nrm[e] = sqrt(a.f.gram[(size_t)m * R * R + r * R + r]);
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double prod = 1.0;
+    for (int m = 0; m < N; ++m) prod *= nrm[m * R + r];
+    const double lam = nth_root(prod, N);
+    for (int m = 0; m < N; ++m) {
+      const double nr = nrm[m * R + r];
+      const double v = nr > 0 ? lam / nr : 1.0;
+      sc[m * R + r] = v;
+      a.f.gram[(size_t)N * R * R + m * R + r] = v;
+    }
+  }
+  __syncthreads();
+  for (int m = 0; m < N; ++m) {
+    const int Im = (int)a.f.I[m];
+    double* Am = a.f.A[m];
+    for (int e = threadIdx.x; e < Im * R; e += blockDim.x) Am[e] *= sc[m * R + e / Im];
+  }
+  for (int e = threadIdx.x; e < N * R * R; e += blockDim.x) {
+    const int m = e / (R * R), rs = e % (R * R);
+    a.f.gram[e] *= sc[m * R + rs / R] * sc[m * R + rs % R];
+  }
+}
+
+// RP: padded rank (4, 8, 12 or 16) sizing the per-row register arrays
+template <int RP>
+__global__ void __launch_bounds__(kMaxThreads) k_finish_update(FuseArgs a) {
+  __shared__ double G[RP * RP], W[RP * RP], V[RP * RP], w[RP], dinv[RP];
+  __shared__ double nrm[kMaxModes * RP], sc[kMaxModes * RP];
+  __shared__ int inv_fail;
   __shared__ bool last;
+  __shared__ double stripe[kMaxThreads];
+  const int nwarps = blockDim.x >> 5;
   const int R = a.f.R;
   const int n = a.n;
   const int64_t I = a.f.I[n];
   double* A = a.f.A[n];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  // Gamma^(n) and its factorization (same arithmetic as the separate ALS / GS kernels)
+  // Gamma^(n): the Hadamard product of the other Grams
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     double v = 1.0;
     for (int m = 0; m < a.f.N; ++m)
       if (m != n) v *= a.f.gram[(size_t)m * R * R + e];
     G[e] = v;
+    W[e] = v;
   }
   __syncthreads();
-  if (threadIdx.x == 0 && a.kind == 0) {
+  if (a.kind == 0) {
     double dmax = 0.0;
     for (int i = 0; i < R; ++i) dmax = fmax(dmax, G[i * R + i]);
-    const double eps = 2.220446049250313e-16;
-    const double thresh = R * eps * (dmax > 0 ? dmax : 1.0);
-    int ok = 1;
-    for (int i = 0; i < R * R; ++i) L[i] = 0.0;
-    for (int j = 0; j < R && ok; ++j) {
-      double s = G[j * R + j];
-      for (int k = 0; k < j; ++k) s -= L[j * R + k] * L[j * R + k];
-      if (!(s > thresh)) { ok = 0; break; }
-      L[j * R + j] = sqrt(s);
-      for (int i = j + 1; i < R; ++i) {
-        double t = G[i * R + j];
-        for (int k = 0; k < j; ++k) t -= L[i * R + k] * L[j * R + k];
-        L[i * R + j] = t / L[j * R + j];
-      }
-    }
-    chol_ok = ok;
-    if (!ok) {
-      double Gc[kR * kR];
-      for (int i = 0; i < R * R; ++i) Gc[i] = G[i];
-      jacobi_eig_dev(Gc, V, w, R);
-      double wmax = 0.0;
-      for (int i = 0; i < R; ++i) wmax = fmax(wmax, fabs(w[i]));
-      const double cut = R * eps * wmax;
-      for (int i = 0; i < R; ++i)
-        for (int j = 0; j < R; ++j) {
-          double s = 0.0;
-          for (int k = 0; k < R; ++k)
-            if (fabs(w[k]) > cut) s += V[i * R + k] * V[j * R + k] / w[k];
-          Pi[i * R + j] = s;
-        }
+    const double thresh = R * 2.220446049250313e-16 * (dmax > 0 ? dmax : 1.0);
+    if (!gj_inverse(W, R, thresh, &inv_fail) && threadIdx.x == 0) {
+      pinv_fallback(G, W, V, w, R);
       if (a.status && blockIdx.x == 0) atomicOr(a.status, 2);
     }
+  } else {
+    for (int r = threadIdx.x; r < R; r += blockDim.x) dinv[r] = 1.0 / G[r * R + r];
   }
   __syncthreads();
 
@@ -98,76 +155,47 @@ __global__ void __launch_bounds__(kWarps * 32) k_finish_update(FuseArgs a) {
   const int64_t rows_per_block = (I + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = blockIdx.x * rows_per_block;
   const int64_t r1 = (r0 + rows_per_block < I) ? r0 + rows_per_block : I;
-  for (int64_t i = r0 + warp; i < r1; i += kWarps) {
-    double s[kR];
+  for (int64_t i = r0 + warp; i < r1; i += nwarps) {
+    double s[RP];
 #pragma unroll
-    for (int r = 0; r < kR; ++r) s[r] = 0.0;
+    for (int r = 0; r < RP; ++r) s[r] = 0.0;
     if (a.first) {
       const int64_t seg = i / a.SEG, ii = i % a.SEG;
       for (int c = lane; c < a.C; c += 32) {
         const int64_t base = ((seg * a.C + c) * a.SEG + ii) * a.RP;
 #pragma unroll
-        for (int r = 0; r < kR; ++r)
+        for (int r = 0; r < RP; ++r)
           if (r < R) s[r] += part_at(a, base + r);
       }
     } else {
-      const int64_t nterm = (int64_t)a.nseg * a.C * a.nw;
-      for (int64_t q = lane; q < nterm; q += 32) {
-        const int64_t u = i * a.nseg * a.C + q / a.nw;
-        const int64_t base = (u * a.nw + q % a.nw) * a.RP;
+      const int nt = a.nseg * a.C * a.nw;
+      const int64_t u0 = i * a.nseg * a.C;
+      for (int q = lane; q < nt; q += 32) {
+        const int64_t base = ((u0 + q / a.nw) * a.nw + q % a.nw) * a.RP;
 #pragma unroll
-        for (int r = 0; r < kR; ++r)
+        for (int r = 0; r < RP; ++r)
           if (r < R) s[r] += part_at(a, base + r);
       }
     }
 #pragma unroll
-    for (int r = 0; r < kR; ++r) {
-      if (r < R) {
-        double v = s[r];
+    for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        s[r] = v;
-      }
+      for (int r = 0; r < RP; ++r)
+        if (r < R) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o);
     }
-    if (lane == 0) {
-      if (a.M)
-        for (int r = 0; r < R; ++r) a.M[i + I * r] = s[r];
-      double x[kR];
-      if (a.kind == 0) {
-        if (chol_ok) {
-          for (int r = 0; r < R; ++r) x[r] = s[r];
-          for (int r = 0; r < R; ++r) {
-            double t = x[r];
-            for (int k = 0; k < r; ++k) t -= L[r * R + k] * x[k];
-            x[r] = t / L[r * R + r];
-          }
-          for (int r = R - 1; r >= 0; --r) {
-            double t = x[r];
-            for (int k = r + 1; k < R; ++k) t -= L[k * R + r] * x[k];
-            x[r] = t / L[r * R + r];
-          }
-        } else {
-          for (int r = 0; r < R; ++r) {
-            double t = 0.0;
-            for (int k = 0; k < R; ++k) t += s[k] * Pi[k * R + r];
-            x[r] = t;
-          }
-        }
-      } else {
-        double b[kR];
-        for (int r = 0; r < R; ++r) {
-          x[r] = A[i + I * r];
-          b[r] = s[r] + (a.F ? a.F[i + I * r] : 0.0);
-        }
-        for (int it = 0; it < a.gs_sweeps; ++it)
-          for (int r = 0; r < R; ++r) {
-            double t = b[r];
-            for (int k = 0; k < R; ++k)
-              if (k != r) t -= G[r * R + k] * x[k];
-            x[r] = t / G[r * R + r];
-          }
+    if (a.M && lane == 0)
+      for (int r = 0; r < R; ++r) a.M[i + I * r] = s[r];
+    if (a.kind == 0) {
+      // A(i, :) = M(i, :) Gamma^+ : lane r forms component r
+      if (lane < R) {
+        double x = 0.0;
+#pragma unroll
+        for (int k = 0; k < RP; ++k)
+          if (k < R) x = __fma_rn(s[k], W[k * R + lane], x);
+        A[i + I * lane] = x;
       }
-      for (int r = 0; r < R; ++r) A[i + I * r] = x[r];
+    } else if (lane == 0) {
+      gs_row(s, a, A, i, I, G, dinv);
     }
   }
   __syncthreads();
@@ -189,21 +217,36 @@ __global__ void __launch_bounds__(kWarps * 32) k_finish_update(FuseArgs a) {
   if (!last) return;
   __threadfence();
   double* Gout = a.f.gram + (size_t)n * R * R;
-  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-    int r = 0, q = p;
-    while (q >= R - r) { q -= R - r; ++r; }
-    const int c = r + q;
-    double acc = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) acc += a.gscratch[(size_t)b * npairs + p];
-    Gout[r * R + c] = acc;
-    Gout[c * R + r] = acc;
+  {
+    // block partials summed in stripes, then the stripes in order (short float64 chains)
+    const int stripes = (int)blockDim.x / npairs > 0 ? (int)blockDim.x / npairs : 1;
+    const int t = threadIdx.x;
+    if (t < stripes * npairs) {
+      const int p = t % npairs, sidx = t / npairs;
+      double acc = 0.0;
+      for (int b = sidx; b < (int)gridDim.x; b += stripes) acc += a.gscratch[(size_t)b * npairs + p];
+      stripe[t] = acc;
+    }
+    __syncthreads();
+    for (int p = t; p < npairs; p += blockDim.x) {
+      int r = 0, q = p;
+      while (q >= R - r) { q -= R - r; ++r; }
+      const int c = r + q;
+      double acc = 0.0;
+      for (int k = 0; k < stripes; ++k) acc += stripe[k * npairs + p];
+      Gout[r * R + c] = acc;
+      Gout[c * R + r] = acc;
+    }
   }
   if (threadIdx.x == 0) *a.ticket = 0;
+  if (!a.normalize) return;
+  __syncthreads();
+  normalize_all(a, nrm, sc);
 }
 
 int launch_finish_update(const MttkrpPlan& p, const MttkrpScratch& w, const FactorSet& f, int mode, int kind,
                          const double* F, int gs_sweeps, double* M, double* gscratch, int* ticket, int* status,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool normalize) {
   FuseArgs a;
   a.f = fargs(f);
   a.n = mode;
@@ -222,9 +265,17 @@ int launch_finish_update(const MttkrpPlan& p, const MttkrpScratch& w, const Fact
   a.gscratch = gscratch;
   a.ticket = ticket;
   a.status = status;
+  a.normalize = normalize ? 1 : 0;
   const int64_t I = f.dims[mode];
-  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((I + kWarps - 1) / kWarps, kFuseMaxBlocks));
-  k_finish_update<<<nb, kWarps * 32, 0, st>>>(a);
+  // few rows per block: GB300's float64 throughput per SM is low, so the per-row reductions and
+  // solves are spread over many SMs (two warps per block when Gamma fits 64 threads)
+  const int threads = f.R * f.R > 64 ? kMaxThreads : 64;
+  const int warps = threads / 32;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((I + warps - 1) / warps, kFuseMaxBlocks));
+  if (f.R <= 4) k_finish_update<4><<<nb, threads, 0, st>>>(a);
+  else if (f.R <= 8) k_finish_update<8><<<nb, threads, 0, st>>>(a);
+  else if (f.R <= 12) k_finish_update<12><<<nb, threads, 0, st>>>(a);
+  else k_finish_update<16><<<nb, threads, 0, st>>>(a);
   CPMG_CUDA_TRY(cudaGetLastError());
   return CPMG_OK;
 }

@@ -12,8 +12,10 @@ constexpr int kFuseMaxBlocks = 256;
 // A^(n) Gamma^(n) = M + F from the current A^(n).  M (optional) receives the reduced MTTKRP.
 // gscratch: kFuseMaxBlocks * R (R + 1) / 2 doubles; ticket: a device int that starts at zero
 // (the kernel returns it to zero).
+// normalize: after the update, Eq. ALSnorm on the whole factor set (scales also written after
+// the Grams, as launch_normalize does).
 int launch_finish_update(const MttkrpPlan& p, const MttkrpScratch& w, const FactorSet& f, int mode, int kind,
                          const double* F, int gs_sweeps, double* M, double* gscratch, int* ticket, int* status,
-                         cudaStream_t st);
+                         cudaStream_t st, bool normalize = false);
 
 }  // namespace cpmg

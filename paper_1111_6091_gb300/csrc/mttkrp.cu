@@ -905,7 +905,7 @@ static size_t main_smem(const MttkrpPlan& p, int block) {
 }
 
 int mttkrp_plan(const Shape& s, int mode, int R, int prec, int zdtype, const void* Z, int num_sms,
-                MttkrpPlan* out, bool allow_tma) {
+                MttkrpPlan* out, bool allow_tma, const MttkrpLimits* lim) {
   if (s.N < 2 || s.N > kMaxModes || mode < 0 || mode >= s.N || R < 1 || R > kMaxRank)
     return CPMG_INVALID_ARG;
   if (prec == P_DF && zdtype != CPMG_F32) prec = P_FP64;  // float64 tensors: native FP64
@@ -946,6 +946,7 @@ int mttkrp_plan(const Shape& s, int mode, int R, int prec, int zdtype, const voi
   p.In = (mode == 0) ? 1 : s.dims[mode];
   const int64_t F = p.Lp * p.G;
   p.TY = (int)std::max<int64_t>(1, std::min<int64_t>(maxthreads / p.TX, F));
+  if (lim && lim->ty > 0) p.TY = std::min(p.TY, lim->ty);
   // TMA staging: columns of whole 16-byte multiples, 16-byte aligned tensor
   const size_t esz = zdtype == CPMG_F64 ? 8 : 4;
   p.use_tma = allow_tma && ((size_t)p.I1 * esz) % 16 == 0 && zp % 16 == 0 &&
@@ -955,6 +956,7 @@ int mttkrp_plan(const Shape& s, int mode, int R, int prec, int zdtype, const voi
     const size_t colbytes = (size_t)p.ROWS * esz;
     // stages of ~48-64 KB: the per-stage hand-off, not the copy engine, limits small stages
     p.CPS = (int)std::max<size_t>(1, std::min<size_t>(8, 65536 / ((size_t)p.TY * colbytes)));
+    if (lim && lim->cps > 0) p.CPS = std::min(p.CPS, lim->cps);
     const size_t SF = (size_t)p.TY * p.CPS;
     p.w_off = (uint32_t)((SF * colbytes + 127) / 128 * 128);
     p.stage_stride = (uint32_t)((p.w_off + SF * p.RP * p.table_bytes + 127) / 128 * 128);

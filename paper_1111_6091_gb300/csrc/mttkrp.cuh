@@ -41,9 +41,15 @@ struct MttkrpPlan {
   size_t tables_bytes() const;  // A1 + Kin + Kout
 };
 
+// Launch-shape limits for mttkrp_plan (0 = the planner's own choice).
+struct MttkrpLimits {
+  int cps = 0;   // columns per column group per stage of the bulk-copy kernel
+  int ty = 0;    // column groups per CTA
+};
+
 // allow_tma = false forces the register-load kernel (smaller scratch: no full row table).
 int mttkrp_plan(const Shape& s, int mode, int R, int prec, int zdtype, const void* Z, int num_sms,
-                MttkrpPlan* p, bool allow_tma = true);
+                MttkrpPlan* p, bool allow_tma = true, const MttkrpLimits* lim = nullptr);
 
 // Device buffers the MTTKRP needs besides Z and the factors.
 struct MttkrpScratch {
