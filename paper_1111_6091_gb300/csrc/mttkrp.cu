@@ -493,7 +493,9 @@ __device__ __forceinline__ void load_z_s(const TZ* p, S* z) {
 // At most four warps land on each SM sub-partition, so 128 (FP32) / 168 registers stay available.
 constexpr int tma_threads(int prec, int RP) { return (prec == P_FP32 && RP <= 12) ? 480 : 288; }
 
-template <typename TZ, int PREC, int VW, int RP, bool FIRST>
+// HP: float pairs actually computed (FP32: ceil(R / 2), so R = 10 runs 5 pairs, not the 6 of the
+// padded table row); other precisions compute all RP.
+template <typename TZ, int PREC, int VW, int RP, bool FIRST, int HP = RP / 2>
 __global__ void __launch_bounds__(tma_threads(PREC, RP), 1) k_mttkrp_tma(TmaArgs ta) {
   using V = typename Tr<PREC>::V;
   using Tab = typename Tr<PREC>::Tab;
@@ -514,17 +516,50 @@ __global__ void __launch_bounds__(tma_threads(PREC, RP), 1) k_mttkrp_tma(TmaArgs
   const int64_t ue = (ta.nunits * (int64_t)(blockIdx.x + 1)) / gridDim.x;
   if (t == 0) {
     for (int s = 0; s < ta.S; ++s) {
-      mbar_init(&full[s], 32);
+      mbar_init(&full[s], ta.contiguous ? 1 : 32);
       mbar_init(&empty[s], nwc);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  constexpr int QA = FIRST ? VW : 1;
+  // FP32 keeps one accumulator per row in every mode (mode n > 1 applies A^(1) once per unit)
+  constexpr int QA = (PREC == P_FP32 || FIRST) ? VW : 1;
   constexpr int QW = FIRST ? 1 : VW;
   bool failed = false;
 
-  if (t >= ncpad) {
+  if (t >= ncpad && ta.contiguous) {
+    // ------------------------------------------------ producer, contiguous stages: one thread
+    // issues one copy of whole columns and one of the matching table rows per stage
+    if (t == ncpad) {
+      const TZ* Z = reinterpret_cast<const TZ*>(a.Z);
+      int s = 0;
+      uint32_t ph = 0;      // parity of the ring's current pass
+      int64_t issued = 0;
+      for (int64_t u = ub; u < ue && !failed; ++u) {
+        const int chunk = (int)(u % a.C);
+        const int64_t in = u / ((int64_t)a.C * a.nseg);
+        const int64_t rows = a.I1 < ta.ROWS ? a.I1 : ta.ROWS;
+        const uint32_t colbytes = (uint32_t)(rows * sizeof(TZ));
+        const int64_t f0 = (a.F * chunk) / a.C, f1 = (a.F * (chunk + 1)) / a.C;
+        // contiguous: mode 1 (f is the column) or the last mode (column f + F * in)
+        const int64_t colbase = (a.In == 1) ? 0 : a.F * in;
+        for (int64_t fs = f0; fs < f1; fs += SF) {
+          if (issued >= ta.S && !mbar_wait(&empty[s], ph ^ 1u)) { failed = true; break; }
+          const int nf = (int)((f1 - fs) < SF ? (f1 - fs) : SF);
+          unsigned char* stage = smem_raw + ta.stage_off + (size_t)s * ta.stage_stride;
+          const uint32_t wbytes = (uint32_t)(nf * RP * sizeof(Tab));
+          mbar_arrive_tx(&full[s], colbytes * (uint32_t)nf + wbytes);
+          bulk_g2s(stage + ta.w_off, wfull + fs * RP, wbytes, &full[s]);
+          bulk_g2s(stage, Z + (colbase + fs) * a.I1, colbytes * (uint32_t)nf, &full[s]);
+          ++issued;
+          if (++s == ta.S) { s = 0; ph ^= 1u; }
+        }
+      }
+      // no copy may still be in flight when shared memory is reused or released
+      for (int64_t j = (issued > ta.S ? issued - ta.S : 0); j < issued; ++j)
+        if (!mbar_wait(&full[j % ta.S], (uint32_t)((j / ta.S) & 1))) failed = true;
+    }
+  } else if (t >= ncpad) {
     // ------------------------------------------------ producer warp: bulk copies only
     const int lane = t - ncpad;
     const TZ* Z = reinterpret_cast<const TZ*>(a.Z);
@@ -588,7 +623,7 @@ __global__ void __launch_bounds__(tma_threads(PREC, RP), 1) k_mttkrp_tma(TmaArgs
     V accm[QA][RP];
     V a1[QW][RP];
     // FP32: packed pairs (the V arrays then only carry the values into the reductions)
-    constexpr int H = (PREC == P_FP32) ? RP / 2 : 1;
+    constexpr int H = (PREC == P_FP32) ? HP : 1;
     unsigned long long acc2[QA][H];
     unsigned long long a1p[QW][H];
 #pragma unroll
@@ -651,34 +686,20 @@ __global__ void __launch_bounds__(tma_threads(PREC, RP), 1) k_mttkrp_tma(TmaArgs
             S zb[VW];
             load_z_s<TZ, VW, S>(reinterpret_cast<const TZ*>(stage + (size_t)k * colbytes) + (int64_t)tx * VW, zb);
             if constexpr (PREC == P_FP32) {
+              // row of the Khatri-Rao table: the HP pairs that are computed
               const ulonglong2* wp = reinterpret_cast<const ulonglong2*>(W + k * RP);
-              unsigned long long w2[RP / 2];
+              unsigned long long w2[2 * ((HP + 1) / 2)];
 #pragma unroll
-              for (int h = 0; h < RP / 4; ++h) {
+              for (int h = 0; h < (HP + 1) / 2; ++h) {
                 const ulonglong2 v = wp[h];
                 w2[2 * h] = v.x;
                 w2[2 * h + 1] = v.y;
               }
-              if constexpr (FIRST) {
 #pragma unroll
-                for (int q = 0; q < VW; ++q) {
-                  const unsigned long long zz = pk2(zb[q], zb[q]);
+              for (int q = 0; q < VW; ++q) {
+                const unsigned long long zz = pk2(zb[q], zb[q]);
 #pragma unroll
-                  for (int h = 0; h < RP / 2; ++h) fma2(acc2[q][h], zz, w2[h]);
-                }
-              } else {
-                unsigned long long u2[RP / 2];
-                const unsigned long long z0 = pk2(zb[0], zb[0]);
-#pragma unroll
-                for (int h = 0; h < RP / 2; ++h) u2[h] = mul2(z0, a1p[0][h]);
-#pragma unroll
-                for (int q = 1; q < QW; ++q) {
-                  const unsigned long long zz = pk2(zb[q], zb[q]);
-#pragma unroll
-                  for (int h = 0; h < RP / 2; ++h) fma2(u2[h], zz, a1p[q][h]);
-                }
-#pragma unroll
-                for (int h = 0; h < RP / 2; ++h) fma2(acc2[0][h], u2[h], w2[h]);
+                for (int h = 0; h < HP; ++h) fma2(acc2[q][h], zz, w2[h]);
               }
             } else {
               V w[RP];
@@ -708,14 +729,26 @@ __global__ void __launch_bounds__(tma_threads(PREC, RP), 1) k_mttkrp_tma(TmaArgs
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
       }
+      // consecutive units of the same output row and row segment accumulate in registers; the
+      // run's total is written to the slot of its last unit, the other slots get zeros
+      const bool run_end = (u + 1 >= ue) || ((u + 1) % a.C == 0);
       if constexpr (!FIRST) {
+       if (!run_end) {
+        Part* zout = reinterpret_cast<Part*>(a.partial) + (u * nwc + warp) * (int64_t)RP;
+        if (lane < RP) zout[lane] = (Part)0;
+       } else {
         if constexpr (PREC == P_FP32) {
+          // sum over this thread's rows of A^(1)(i_1, r) * (sum over columns of z * w)
 #pragma unroll
           for (int h = 0; h < H; ++h) {
-            const float2 f = up2(acc2[0][h]);
+            unsigned long long r2 = mul2(acc2[0][h], a1p[0][h]);
+#pragma unroll
+            for (int q = 1; q < VW; ++q) fma2(r2, acc2[q][h], a1p[q][h]);
+            const float2 f = up2(r2);
             accm[0][2 * h] = f.x;
             accm[0][2 * h + 1] = f.y;
-            acc2[0][h] = 0ull;
+#pragma unroll
+            for (int q = 0; q < VW; ++q) acc2[q][h] = 0ull;
           }
         }
         // per-warp partial of this unit: partial[(u * nwc + warp) * RP + r]
@@ -730,6 +763,7 @@ __global__ void __launch_bounds__(tma_threads(PREC, RP), 1) k_mttkrp_tma(TmaArgs
           if (lane == 0) out[r] = v;
           accm[0][r] = Ops<V>::zero();
         }
+       }
       }
     }
     if constexpr (FIRST) {
@@ -873,7 +907,17 @@ static void raise_smem_cap(Fn fn) {
 }
 
 template <typename TZ, int PREC, int VW, bool FIRST>
-static TmaFn tma_rp1(int RP) {
+static TmaFn tma_rp1(int RP, int R) {
+  if constexpr (PREC == P_FP32) {
+    // odd ranks run one pair fewer than the padded row holds
+    const bool odd_less = (R + 1) / 2 < RP / 2;
+    switch (RP) {
+      case 4: return odd_less ? k_mttkrp_tma<TZ, PREC, VW, 4, FIRST, 1> : k_mttkrp_tma<TZ, PREC, VW, 4, FIRST, 2>;
+      case 8: return odd_less ? k_mttkrp_tma<TZ, PREC, VW, 8, FIRST, 3> : k_mttkrp_tma<TZ, PREC, VW, 8, FIRST, 4>;
+      case 12: return odd_less ? k_mttkrp_tma<TZ, PREC, VW, 12, FIRST, 5> : k_mttkrp_tma<TZ, PREC, VW, 12, FIRST, 6>;
+      default: return odd_less ? k_mttkrp_tma<TZ, PREC, VW, 16, FIRST, 7> : k_mttkrp_tma<TZ, PREC, VW, 16, FIRST, 8>;
+    }
+  }
   switch (RP) {
     case 4: return k_mttkrp_tma<TZ, PREC, VW, 4, FIRST>;
     case 8: return k_mttkrp_tma<TZ, PREC, VW, 8, FIRST>;
@@ -884,7 +928,7 @@ static TmaFn tma_rp1(int RP) {
 
 template <typename TZ, int PREC, int VW>
 static TmaFn tma_rp(const MttkrpPlan& p) {
-  return p.mode == 0 ? tma_rp1<TZ, PREC, VW, true>(p.RP) : tma_rp1<TZ, PREC, VW, false>(p.RP);
+  return p.mode == 0 ? tma_rp1<TZ, PREC, VW, true>(p.RP, p.R) : tma_rp1<TZ, PREC, VW, false>(p.RP, p.R);
 }
 
 static TmaFn pick_tma(const MttkrpPlan& p) {
