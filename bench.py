@@ -505,6 +505,40 @@ def run_ttm_case(args):
     ctx.close()
 
 
+def run_sweep_case(args):
+    """Small case for launch-list captures: 20 FP32 and 20 float-pair ALS sweeps of the 100^3
+    rank-5 workload tensor (about 250 kernel launches)."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    p = problem()
+    stream = torch.cuda.Stream()
+    ctx = cpmg.Context(0, stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        Z = cpmg.colmajor(p.Z)
+        A = [cpmg.colmajor(a) for a in p.A0]
+        for prec in (cpmg.PREC_FP32, cpmg.PREC_DF):
+            cpmg.cp_als_sweep(ctx, Z, A, 20, precision=prec, check_every=0)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "als sweeps 100^3 R=5", "sweeps": 40}))
+    ctx.close()
+
+
+def run_batch_case(args):
+    """Small case for profiler captures: 64 tensors of the uneven batch workload, 16 MIXED
+    sweeps each in one batched solve (two launches of the persistent kernel)."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    probs = batch_problems(64)
+    ctx = cpmg.Context(0)
+    Zs = [cpmg.colmajor(p.Z) for p in probs]
+    As = [[cpmg.colmajor(a) for a in p.A0] for p in probs]
+    st, res = cpmg.cpmg_batch_solve(ctx, Zs, As, precision=cpmg.PREC_MIXED, tol=0.0, max_als_iters=16,
+                                    check_every=8)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "batched 64 tensors", "sweeps": sum(r["iters_als"] for r in res)}))
+    ctx.close()
+
+
 def run_mttkrp_case(args):
     """Small case for profiler captures: two FP32 ALS sweeps on the 400^3 rank-10 tensor
     (six MTTKRP main-kernel launches)."""
@@ -526,6 +560,8 @@ def main():
     ap.add_argument("--mttkrp-case", action="store_true", help="profiler case: 2 sweeps at 400^3")
     ap.add_argument("--case-prec", default="fp32", choices=["fp32", "df", "fp64"])
     ap.add_argument("--ttm-case", action="store_true", help="profiler case: one 400^3 restriction")
+    ap.add_argument("--sweep-case", action="store_true", help="profiler case: 40 ALS sweeps at 100^3")
+    ap.add_argument("--batch-case", action="store_true", help="profiler case: a 64-tensor batched solve")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -533,7 +569,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-only", action="store_true", help="profiler case: the timed solves only")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT, help="batched workload size (0: skip)")
-    ap.add_argument("--serve-requests", type=int, default=2000,
+    ap.add_argument("--serve-requests", type=int, default=1000,
                     help="requests of the served workload (20000 for the full stream; 0: skip)")
     args = ap.parse_args()
     if args.impl != "reference":
@@ -543,6 +579,10 @@ def main():
         run_mttkrp_case(args)
     elif args.ttm_case:
         run_ttm_case(args)
+    elif args.sweep_case:
+        run_sweep_case(args)
+    elif args.batch_case:
+        run_batch_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

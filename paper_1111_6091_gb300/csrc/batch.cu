@@ -109,6 +109,16 @@ __device__ __forceinline__ double bto_d(float x) { return (double)x; }
 __device__ __forceinline__ double bto_d(double x) { return x; }
 __device__ __forceinline__ double bto_d(df x) { return df_to_double(x); }
 
+// w *= a (a float64 factor entry) in the compute precision: float products for FP32, float
+// pairs for the float64-accurate path (GB300's float64 pipe is narrow; this runs per column)
+__device__ __forceinline__ void bwmul(float& w, double a) { w *= (float)a; }
+__device__ __forceinline__ void bwmul(double& w, double a) { w *= a; }
+__device__ __forceinline__ void bwmul(df& w, double a) { w = df_mul(w, df_from_double(a)); }
+template <typename V> __device__ __forceinline__ V bone();
+template <> __device__ __forceinline__ float bone<float>() { return 1.f; }
+template <> __device__ __forceinline__ double bone<double>() { return 1.0; }
+template <> __device__ __forceinline__ df bone<df>() { return {1.f, 0.f}; }
+
 // a * y in the compute precision, returned as float64 (the cross-lane sums run in float64)
 __device__ __forceinline__ double bmul_d(double a, float y) { return (double)((float)a * y); }
 __device__ __forceinline__ double bmul_d(double a, double y) { return a * y; }
@@ -175,9 +185,9 @@ __device__ void unit_run(const BTen& T, const BUnit& u, int lane, void* wsv, int
       const int64_t j = jb + lane;
       const int64_t col = (n == 0) ? j : (j % Lp) + Lp * (u.in_idx + In * (j / Lp));
       wc[lane] = col;
-      double w[kBR];
+      V w[kBR];
 #pragma unroll
-      for (int r = 0; r < kBR; ++r) w[r] = 1.0;
+      for (int r = 0; r < kBR; ++r) w[r] = bone<V>();
       int64_t rem = col;
       for (int m = 1; m < N; ++m) {
         const int64_t Im = T.dims[m];
@@ -187,11 +197,11 @@ __device__ void unit_run(const BTen& T, const BUnit& u, int lane, void* wsv, int
           const double* Am = T.A[m];
 #pragma unroll
           for (int r = 0; r < kBR; ++r)
-            if (r < R) w[r] *= Am[im + Im * r];
+            if (r < R) bwmul(w[r], Am[im + Im * r]);
         }
       }
 #pragma unroll
-      for (int r = 0; r < kBR; ++r) ws[lane * kBR + r] = (r < R) ? bconv<V>(w[r]) : bzero<V>();
+      for (int r = 0; r < kBR; ++r) ws[lane * kBR + r] = (r < R) ? w[r] : bzero<V>();
     }
     __syncwarp();
     for (int jj = 0; jj < cnt; ++jj) {
@@ -530,10 +540,26 @@ __global__ void __launch_bounds__(kBThreads) k_batch_init(BTen* ten, int nten) {
     if (!T.init) continue;
     int64_t P = 1;
     for (int m = 0; m < T.N; ++m) P *= T.dims[m];
+    // ||Z||^2: float tensors square and sum in float pairs (exact products, error-free sums),
+    // four loads in flight per thread
     double s = 0.0;
-    for (int64_t e = threadIdx.x; e < P; e += blockDim.x) {
-      const double z = T.zf64 ? reinterpret_cast<const double*>(T.Z)[e] : (double)reinterpret_cast<const float*>(T.Z)[e];
-      s += z * z;
+    if (T.zf64) {
+      const double* Zd = reinterpret_cast<const double*>(T.Z);
+      for (int64_t e = threadIdx.x; e < P; e += blockDim.x) s += Zd[e] * Zd[e];
+    } else {
+      const float* Zf = reinterpret_cast<const float*>(T.Z);
+      df acc = {0.f, 0.f};
+      for (int64_t e0 = threadIdx.x; e0 < P; e0 += 4 * (int64_t)blockDim.x) {
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int64_t e = e0 + (int64_t)k * blockDim.x;
+          v[k] = e < P ? Zf[e] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc = df_add(acc, df_mul_f(v[k], {v[k], 0.f}));
+      }
+      s = df_to_double(acc);
     }
     const double zz = bblock_sum(s, buf);
     for (int m = 0; m < T.N; ++m) gram_rows(T.A[m], T.dims[m], T.R, T.gram + m * kGramStride, buf);
