@@ -48,6 +48,8 @@ struct BTen {
   const void* Z;
   double* A[kBModes];
   double* gram;                 // kBModes x 8 x 8
+  double* ginv;                 // 8 x 8: (Gamma^(n))^+ of the next mode to update
+  double* rowres;               // per mode and row: ||A Gamma - M||^2, ||M||^2, <M, A> (g evaluation)
   double* part[kBModes];        // partial sums of the MTTKRP of each mode
   int64_t dims[kBModes];
   int nk[kBModes];              // partial slots per output row (mode > 0) or column chunks (mode 0)
@@ -71,11 +73,20 @@ struct BUnit {
   int64_t in_idx;               // i_n (mode > 0)
 };
 
+// kBRowsPerItem consecutive output rows of one mode of one tensor (one warp per row)
+constexpr int kBRowsPerItem = kBThreads / 32;
+struct BRow {
+  int t, mode;
+  int64_t r0;
+};
+
 struct BArgs {
   BTen* ten;
   int nten;
   const BUnit* units[kBModes];
   int64_t nunits[kBModes];
+  const BRow* rows[kBModes];    // row items per mode
+  int64_t nrows[kBModes];
   int maxN;
   int nsweeps;
   int eval;                     // 1: evaluate g and decide; 2: MTTKRP phases only (autotuner)
@@ -256,10 +267,10 @@ __device__ void unit_run(const BTen& T, const BUnit& u, int lane, void* wsv, int
 struct BSmem {
   double ws[kBWarps][32 * kBR];   // Khatri-Rao rows of 32 columns (float / double / df)
   int64_t wc[kBWarps][32];
-  double G[kBR * kBR], L[kBR * kBR], Pi[kBR * kBR], V[kBR * kBR], w[kBR];
+  double G[kBR * kBR], Pi[kBR * kBR], V[kBR * kBR], w[kBR];
   double red[3][kBThreads];
   double sc[kBModes][kBR];
-  int chol_ok;
+  int fail;
 };
 
 __device__ void phase_units(const BArgs& a, int n, bool eval, BSmem& sm) {
@@ -277,23 +288,29 @@ __device__ void phase_units(const BArgs& a, int n, bool eval, BSmem& sm) {
   }
 }
 
-// M^(n) row i from the partials, in a fixed order
-__device__ __forceinline__ void row_sum(const BTen& T, int n, int64_t i, double* m) {
+// M^(n) row i from the partials: lanes take terms lane, lane + 32, ..., then a fixed butterfly;
+// every lane ends with the whole row (fixed order, so reproducible)
+__device__ __forceinline__ void row_sum_warp(const BTen& T, int n, int64_t i, int lane, double* m) {
 #pragma unroll
   for (int r = 0; r < kBR; ++r) m[r] = 0.0;
+  const int nk = T.nk[n];
   if (n == 0) {
     const int64_t I0 = T.dims[0];
-    for (int k = 0; k < T.nk[0]; ++k) {
+    for (int k = lane; k < nk; k += 32) {
       const double* p = T.part[0] + ((int64_t)k * I0 + i) * kBR;
 #pragma unroll
       for (int r = 0; r < kBR; ++r) m[r] += p[r];
     }
   } else {
-    const double* p = T.part[n] + (i * T.nk[n]) * kBR;
-    for (int k = 0; k < T.nk[n]; ++k)
+    const double* p = T.part[n] + (i * nk) * kBR;
+    for (int k = lane; k < nk; k += 32)
 #pragma unroll
       for (int r = 0; r < kBR; ++r) m[r] += p[(int64_t)k * kBR + r];
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) m[r] += __shfl_xor_sync(0xffffffffu, m[r], o);
 }
 
 // deterministic block sum of one value per thread (thread 0 adds in thread order)
@@ -347,13 +364,28 @@ __device__ void gram_rows(const double* A, int64_t I, int R, double* gram, doubl
   __syncthreads();
 }
 
-// update: the ALS update of mode n and its Gram.  !update: ||A Gamma - M||^2, ||M||^2 (and
-// <M, A> for the last mode) at the current factors.
-__device__ void finish_tensor(BTen& T, int n, bool update, BSmem& sm) {
-  const int R = T.R, N = T.N, tid = threadIdx.x;
-  const int64_t In = T.dims[n];
-  double* A = T.A[n];
-  for (int e = tid; e < R * R; e += blockDim.x) {
+// singular Gamma (thread 0): Pi = Gamma^+ from a symmetric eigendecomposition
+__device__ __noinline__ void bpinv(const double* G, double* Pi, double* V, double* w, int R) {
+  const double eps = 2.220446049250313e-16;
+  double Gc[kBR * kBR];
+  for (int i = 0; i < R * R; ++i) Gc[i] = G[i];
+  jacobi_eig_dev(Gc, V, w, R);
+  double wmax = 0.0;
+  for (int i = 0; i < R; ++i) wmax = fmax(wmax, fabs(w[i]));
+  const double cut = R * eps * wmax;
+  for (int i = 0; i < R; ++i)
+    for (int j = 0; j < R; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < R; ++k)
+        if (fabs(w[k]) > cut) s += V[i * R + k] * V[j * R + k] / w[k];
+      Pi[i * R + j] = s;
+    }
+}
+
+// T.ginv = (Gamma^(n))^+ with Gamma^(n) the Hadamard product of the other Grams (block-wide)
+__device__ void gamma_inverse(BTen& T, int n, BSmem& sm) {
+  const int R = T.R, N = T.N;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     double v = 1.0;
     for (int m = 0; m < N; ++m)
       if (m != n) v *= T.gram[m * kGramStride + (e / R) * kBR + (e % R)];
@@ -361,74 +393,16 @@ __device__ void finish_tensor(BTen& T, int n, bool update, BSmem& sm) {
     sm.Pi[e] = v;
   }
   __syncthreads();
-  if (update) {
-    double dmax = 0.0;
-    for (int i = 0; i < R; ++i) dmax = fmax(dmax, sm.G[i * R + i]);
-    const double eps = 2.220446049250313e-16;
-    const double thresh = R * eps * (dmax > 0 ? dmax : 1.0);
-    if (!gj_inverse(sm.Pi, R, thresh, &sm.chol_ok)) {
-      // singular Gamma: the pseudoinverse from a symmetric eigendecomposition
-      if (tid == 0) {
-        double Gc[kBR * kBR];
-        for (int i = 0; i < R * R; ++i) Gc[i] = sm.G[i];
-        jacobi_eig_dev(Gc, sm.V, sm.w, R);
-        double wmax = 0.0;
-        for (int i = 0; i < R; ++i) wmax = fmax(wmax, fabs(sm.w[i]));
-        const double cut = R * eps * wmax;
-        for (int i = 0; i < R; ++i)
-          for (int j = 0; j < R; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < R; ++k)
-              if (fabs(sm.w[k]) > cut) s += sm.V[i * R + k] * sm.V[j * R + k] / sm.w[k];
-            sm.Pi[i * R + j] = s;
-          }
-      }
-    }
-    __syncthreads();
-  }
-  double res = 0.0, m2 = 0.0, zin = 0.0;
-  for (int64_t i = tid; i < In; i += blockDim.x) {
-    double m[kBR];
-    row_sum(T, n, i, m);
-    if (update) {
-#pragma unroll
-      for (int r = 0; r < kBR; ++r) {
-        if (r < R) {
-          double x = 0.0;
-#pragma unroll
-          for (int k = 0; k < kBR; ++k)
-            if (k < R) x = __fma_rn(m[k], sm.Pi[k * R + r], x);
-          A[i + In * r] = x;
-        }
-      }
-    } else {
-      for (int r = 0; r < R; ++r) {
-        double ag = 0.0;
-        for (int k = 0; k < R; ++k) ag += A[i + In * k] * sm.G[k * R + r];
-        const double d = ag - m[r];
-        res += d * d;
-        m2 += m[r] * m[r];
-        zin += m[r] * A[i + In * r];
-      }
-    }
-  }
+  double dmax = 0.0;
+  for (int i = 0; i < R; ++i) dmax = fmax(dmax, sm.G[i * R + i]);
+  const double thresh = R * 2.220446049250313e-16 * (dmax > 0 ? dmax : 1.0);
+  if (!gj_inverse(sm.Pi, R, thresh, &sm.fail) && threadIdx.x == 0) bpinv(sm.G, sm.Pi, sm.V, sm.w, R);
   __syncthreads();
-  if (update) {
-    gram_rows(A, In, R, T.gram + n * kGramStride, sm.red[0]);
-  } else {
-    const double s_res = bblock_sum(res, sm.red[0]);
-    const double s_m2 = bblock_sum(m2, sm.red[1]);
-    const double s_zin = bblock_sum(zin, sm.red[2]);
-    if (tid == 0) {
-      T.res2[n] = s_res;
-      T.m2[n] = s_m2;
-      if (n == N - 1) T.zin = s_zin;
-    }
-  }
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) T.ginv[(e / R) * kBR + (e % R)] = sm.Pi[e];
   __syncthreads();
 }
 
-// Eq. ALSnorm with the column norms taken from the Gram diagonals
+// Eq. ALSnorm with the column norms taken from the Gram diagonals (block-wide)
 __device__ void normalize_tensor(BTen& T, BSmem& sm) {
   const int R = T.R, N = T.N, tid = threadIdx.x;
   for (int e = tid; e < N * R; e += blockDim.x) {
@@ -447,8 +421,8 @@ __device__ void normalize_tensor(BTen& T, BSmem& sm) {
   }
   __syncthreads();
   for (int m = 0; m < N; ++m) {
-    const int64_t Im = T.dims[m];
-    for (int64_t e = tid; e < Im * R; e += blockDim.x) T.A[m][e] *= sm.sc[m][e / Im];
+    const int Im = (int)T.dims[m];
+    for (int e = tid; e < Im * R; e += blockDim.x) T.A[m][e] *= sm.sc[m][e / Im];
     for (int e = tid; e < R * R; e += blockDim.x) {
       const int r = e / R, c = e % R;
       T.gram[m * kGramStride + r * kBR + c] *= sm.sc[m][r] * sm.sc[m][c];
@@ -457,6 +431,67 @@ __device__ void normalize_tensor(BTen& T, BSmem& sm) {
   __syncthreads();
   if (tid == 0) T.iters += 1;
   __syncthreads();
+}
+
+// rows of mode n (or of every mode for the g evaluation): one warp per row.  update: the ALS
+// row A(i,:) = M(i,:) Gamma^+ (lane r forms component r).  !update: the row's contributions to
+// ||A Gamma - M||^2, ||M||^2 and <M, A>, stored per row for an ordered sum.
+__device__ void phase_rows(const BArgs& a, const BRow* items, int64_t nitems, bool update) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BRow rw = items[it];
+    const BTen& T = a.ten[rw.t];
+    if (!T.active) continue;
+    const int n = rw.mode, R = T.R, N = T.N;
+    const int64_t In = T.dims[n];
+    const int64_t i = rw.r0 + warp;
+    if (i >= In) continue;
+    double m[kBR];
+    row_sum_warp(T, n, i, lane, m);
+    double* A = T.A[n];
+    if (update) {
+      if (lane < R) {
+        double x = 0.0;
+#pragma unroll
+        for (int k = 0; k < kBR; ++k)
+          if (k < R) x = __fma_rn(m[k], T.ginv[k * kBR + lane], x);
+        A[i + In * lane] = x;
+      }
+    } else {
+      double res = 0.0, mm = 0.0, zi = 0.0;
+      if (lane < R) {
+        double ag = 0.0;
+        for (int k = 0; k < R; ++k) {
+          double gk = 1.0;
+          for (int q = 0; q < N; ++q)
+            if (q != n) gk *= T.gram[q * kGramStride + k * kBR + lane];
+          ag = __fma_rn(A[i + In * k], gk, ag);
+        }
+        double mr = 0.0;
+#pragma unroll
+        for (int r = 0; r < kBR; ++r)
+          if (r == lane) mr = m[r];
+        const double d = ag - mr;
+        res = d * d;
+        mm = mr * mr;
+        zi = mr * A[i + In * lane];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        res += __shfl_xor_sync(0xffffffffu, res, o);
+        mm += __shfl_xor_sync(0xffffffffu, mm, o);
+        zi += __shfl_xor_sync(0xffffffffu, zi, o);
+      }
+      if (lane == 0) {
+        int64_t off = 0;
+        for (int q = 0; q < n; ++q) off += T.dims[q];
+        double* rr = T.rowres + 3 * (off + i);
+        rr[0] = res;
+        rr[1] = mm;
+        rr[2] = zi;
+      }
+    }
+  }
 }
 
 __device__ void check_tensor(BTen& T, int* nactive, BSmem& sm) {
@@ -469,6 +504,28 @@ __device__ void check_tensor(BTen& T, int* nactive, BSmem& sm) {
     part += p;
   }
   const double cross = bblock_sum(part, sm.red[0]);
+  // per-mode sums of the row contributions, in row order within stripes
+  int64_t off = 0;
+  for (int n = 0; n < T.N; ++n) {
+    const int64_t In = T.dims[n];
+    double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+    for (int64_t i = threadIdx.x; i < In; i += blockDim.x) {
+      const double* rr = T.rowres + 3 * (off + i);
+      r0 += rr[0];
+      r1 += rr[1];
+      r2 += rr[2];
+    }
+    const double s0 = bblock_sum(r0, sm.red[0]);
+    const double s1 = bblock_sum(r1, sm.red[1]);
+    const double s2 = bblock_sum(r2, sm.red[2]);
+    if (threadIdx.x == 0) {
+      T.res2[n] = s0;
+      T.m2[n] = s1;
+      if (n == T.N - 1) T.zin = s2;
+    }
+    off += In;
+  }
+  __syncthreads();
   if (threadIdx.x != 0) return;
   double g2 = 0.0, m2 = 0.0;
   for (int n = 0; n < T.N; ++n) {
@@ -509,21 +566,29 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BArgs a) {
     for (int n = 0; n < a.maxN && ok; ++n) {
       phase_units(a, n, false, sm);
       ok = grid_sync(a.bar, a.err);
-      for (int t = blockIdx.x; t < a.nten && ok; t += gridDim.x)
-        if (a.ten[t].active && n < a.ten[t].N) finish_tensor(a.ten[t], n, true, sm);
+      if (ok) phase_rows(a, a.rows[n], a.nrows[n], true);
+      ok = ok && grid_sync(a.bar, a.err);
+      // per tensor: the Gram of the new A^(n); after the last mode Eq. ALSnorm; then Gamma^+
+      // of the next mode to update
+      for (int t = blockIdx.x; t < a.nten && ok; t += gridDim.x) {
+        BTen& T = a.ten[t];
+        if (!T.active || n >= T.N) continue;
+        gram_rows(T.A[n], T.dims[n], T.R, T.gram + n * kGramStride, sm.red[0]);
+        const bool last_mode = n == T.N - 1;
+        if (last_mode) normalize_tensor(T, sm);
+        gamma_inverse(T, last_mode ? 0 : n + 1, sm);
+      }
       ok = ok && grid_sync(a.bar, a.err);
     }
-    for (int t = blockIdx.x; t < a.nten && ok; t += gridDim.x)
-      if (a.ten[t].active) normalize_tensor(a.ten[t], sm);
-    ok = ok && grid_sync(a.bar, a.err);
   }
   if (a.eval && ok) {
     for (int n = 0; n < a.maxN; ++n) phase_units(a, n, a.eval == 1, sm);
     ok = grid_sync(a.bar, a.err);
-    if (a.eval == 1) {
+    if (a.eval == 1 && ok) {
+      for (int n = 0; n < a.maxN; ++n) phase_rows(a, a.rows[n], a.nrows[n], false);
+      ok = grid_sync(a.bar, a.err);
       for (int t = blockIdx.x; t < a.nten && ok; t += gridDim.x) {
         if (!a.ten[t].active) continue;
-        for (int n = 0; n < a.ten[t].N; ++n) finish_tensor(a.ten[t], n, false, sm);
         check_tensor(a.ten[t], a.nactive, sm);
         __syncthreads();
       }
@@ -532,8 +597,9 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BArgs a) {
 }
 
 // ------------------------------------------------------------------ setup / final kernels
-// ||Z||^2 and the Grams of every tensor (block per tensor, fixed order)
+// ||Z||^2, the Grams and Gamma^(1)^+ of every tensor still to initialize (block per tensor)
 __global__ void __launch_bounds__(kBThreads) k_batch_init(BTen* ten, int nten) {
+  __shared__ BSmem sm;
   __shared__ double buf[kBThreads];
   for (int t = blockIdx.x; t < nten; t += gridDim.x) {
     BTen& T = ten[t];
@@ -563,6 +629,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch_init(BTen* ten, int nten) {
     }
     const double zz = bblock_sum(s, buf);
     for (int m = 0; m < T.N; ++m) gram_rows(T.A[m], T.dims[m], T.R, T.gram + m * kGramStride, buf);
+    gamma_inverse(T, 0, sm);
     if (threadIdx.x == 0) {
       T.znorm2 = zz;
       T.init = 0;
@@ -625,7 +692,7 @@ struct BItem {                   // one problem as given by the caller
   int zf64, N, R;
   int64_t dims[kBModes];
   double* A[kBModes];            // device float64 factors, updated in place
-  double* gram;                  // device kBModes x 8 x 8, owned by the batch or the request
+  double* gram;                  // device block of aux_doubles(): Grams, Gamma^+, row sums
   cpmg_opts o;
   int64_t target;                // elements per MTTKRP unit (autotuned per shape class)
   bool has_state;
@@ -679,6 +746,13 @@ static void plan_units(const std::vector<BItem>& items, std::vector<BUnit>* unit
   *part_total = off;
 }
 
+// per-tensor device state besides the factors: kBModes Grams, one Gamma^+, 3 doubles per row
+static size_t aux_doubles(const BItem& it) {
+  int64_t rows = 0;
+  for (int m = 0; m < it.N; ++m) rows += it.dims[m];
+  return (size_t)(kBModes + 1) * kGramStride + 3 * (size_t)rows;
+}
+
 static size_t partial_doubles_of(const BItem& it) {
   std::vector<BItem> one(1, it);
   std::vector<BUnit> u[kBModes];
@@ -699,6 +773,8 @@ static BTen make_desc(const BItem& it) {
     T.part[m] = nullptr;
   }
   T.gram = it.gram;
+  T.ginv = it.gram + kBModes * kGramStride;
+  T.rowres = T.ginv + kGramStride;
   T.N = it.N;
   T.R = it.R;
   T.zf64 = it.zf64;
@@ -731,6 +807,9 @@ struct BatchDev {
   BUnit* d_units[kBModes] = {nullptr, nullptr, nullptr, nullptr};
   size_t cap_units[kBModes] = {0, 0, 0, 0};
   int64_t nunits[kBModes] = {0, 0, 0, 0};
+  BRow* d_rows[kBModes] = {nullptr, nullptr, nullptr, nullptr};
+  size_t cap_rows[kBModes] = {0, 0, 0, 0};
+  int64_t nrows[kBModes] = {0, 0, 0, 0};
   double* d_part = nullptr;
   size_t cap_part = 0;
   int* d_idx = nullptr;
@@ -743,6 +822,7 @@ struct BatchDev {
   void release() {
     if (!c) return;
     for (int n = 0; n < kBModes; ++n) ctx_free(c, d_units[n]), d_units[n] = nullptr, cap_units[n] = 0;
+    for (int n = 0; n < kBModes; ++n) ctx_free(c, d_rows[n]), d_rows[n] = nullptr, cap_rows[n] = 0;
     ctx_free(c, d_ten);
     ctx_free(c, d_part);
     ctx_free(c, d_idx);
@@ -805,6 +885,18 @@ static int batch_load(BatchDev& B, const std::vector<BItem>& items) {
     CPMG_CUDA_TRY(cudaMemcpyAsync(B.d_units[n], units[n].data(), units[n].size() * sizeof(BUnit),
                                   cudaMemcpyHostToDevice, st));
   }
+  // row items: kBRowsPerItem output rows of one mode of one tensor
+  std::vector<BRow> rows[kBModes];
+  for (size_t t = 0; t < items.size(); ++t)
+    for (int n = 0; n < items[t].N; ++n)
+      for (int64_t r0 = 0; r0 < items[t].dims[n]; r0 += kBRowsPerItem) rows[n].push_back({(int)t, n, r0});
+  for (int n = 0; n < kBModes; ++n) {
+    B.nrows[n] = (int64_t)rows[n].size();
+    if (rows[n].empty()) continue;
+    CPMG_TRY(grow(B.c, &B.d_rows[n], &B.cap_rows[n], rows[n].size()));
+    CPMG_CUDA_TRY(cudaMemcpyAsync(B.d_rows[n], rows[n].data(), rows[n].size() * sizeof(BRow),
+                                  cudaMemcpyHostToDevice, st));
+  }
   B.host.resize(items.size());
   bool any_init = false;
   for (size_t t = 0; t < items.size(); ++t) {
@@ -834,6 +926,8 @@ static int launch_batch(BatchDev& B, int nsweeps, int eval) {
   for (int n = 0; n < kBModes; ++n) {
     a.units[n] = B.d_units[n];
     a.nunits[n] = B.nunits[n];
+    a.rows[n] = B.d_rows[n];
+    a.nrows[n] = B.nrows[n];
   }
   a.maxN = B.maxN;
   a.nsweeps = nsweeps;
@@ -1047,7 +1141,7 @@ static void server_loop(cpmg_ctx* c, BatchState* S) {
     for (auto* q : admitted)
       if (!q->item.gram) {
         void* g = nullptr;
-        if ((rc = ctx_alloc(c, &g, kBModes * kGramStride * sizeof(double))) != CPMG_OK) break;
+        if ((rc = ctx_alloc(c, &g, aux_doubles(q->item) * sizeof(double))) != CPMG_OK) break;
         q->item.gram = reinterpret_cast<double*>(g);
       }
     if (rc != CPMG_OK) break;
@@ -1156,10 +1250,15 @@ int cpmg_batch_solve(cpmg_ctx* c, int count, const cpmg_tensor* Z, const int* R,
   BatchDev B;
   double* grams = nullptr;
   int st = batch_open(c, B);
-  if (st == CPMG_OK)
-    st = ctx_alloc(c, reinterpret_cast<void**>(&grams), (size_t)count * kBModes * kGramStride * sizeof(double));
+  size_t aux_total = 0;
+  for (int t = 0; t < count; ++t) aux_total += aux_doubles(items[t]);
+  if (st == CPMG_OK) st = ctx_alloc(c, reinterpret_cast<void**>(&grams), aux_total * sizeof(double));
   if (st == CPMG_OK) {
-    for (int t = 0; t < count; ++t) items[t].gram = grams + (size_t)t * kBModes * kGramStride;
+    size_t off = 0;
+    for (int t = 0; t < count; ++t) {
+      items[t].gram = grams + off;
+      off += aux_doubles(items[t]);
+    }
     st = autotune(B, items);
   }
   if (st == CPMG_OK) st = batch_load(B, items);
@@ -1215,7 +1314,7 @@ int cpmg_server_submit(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* 
   const int64_t P = numel_of(it);
   size_t fb = 0;
   for (int m = 0; m < it.N; ++m) fb += (size_t)it.dims[m] * R * 8;
-  q->bytes = (size_t)P * (it.zf64 ? 8 : 4) + fb + partial_doubles_of(it) * 8 + kBModes * kGramStride * 8;
+  q->bytes = (size_t)P * (it.zf64 ? 8 : 4) + fb + partial_doubles_of(it) * 8 + aux_doubles(it) * 8;
   std::unique_lock<std::mutex> lk(S->mu);
   if (S->budget && q->bytes > S->budget) {
     delete q;
