@@ -226,9 +226,9 @@ int cpmg_decompose(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A,
 /* CP-ALS (Section 3: for n = 1..N, A^(n) <- Z_(n) Phi^(n) (Gamma^(n))^+, then Eq. ALSnorm;
  * components sorted by decreasing lambda at the end) on `count` independent tensors at once,
  * each stopping when its g of Eq. gradConv drops below opts->tol or after opts->max_als_iters
- * sweeps.  Z[t]: device tensor, order 2..4, float32 or float64; R[t] in 1..8; A[t]: Z[t].N
- * device float64 I_n x R column-major factor arrays (initial guess in, result out), owned by
- * the caller and not aliased between tensors.  opts: precision (FP32 / DF / MIXED / FP64, as
+ * sweeps.  Z[t]: device tensor, order 2..4, float32 or float64, fewer than 2^32 elements;
+ * R[t] in 1..8; A[t]: Z[t].N device float64 I_n x R column-major factor arrays (initial
+ * guess in, result out), owned by the caller and not aliased between tensors.  opts: precision (FP32 / DF / MIXED / FP64, as
  * for cp_als_sweep), tol, max_als_iters, mixed_switch; check_every > 0 = sweeps between
  * g evaluations (default 8 when <= 0; the last evaluation may come up to check_every - 1 sweeps
  * after g first fell below tol).  All sweeps of all tensors run in one cooperative persistent

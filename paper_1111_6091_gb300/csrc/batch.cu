@@ -5,17 +5,21 @@
 // One cooperative, persistent kernel runs k whole sweeps of every active tensor followed by one
 // g evaluation.  Inside it, phases are separated by a grid barrier (bounded wait):
 //   units(n)   warps walk the list of MTTKRP work units of mode n of all tensors; a unit is
-//              (tensor, block of 64 rows of the first mode, chunk of columns) and writes float64
-//              partial sums to a slot of its own, so each tensor's arithmetic is independent of
-//              what else is in the batch
-//   finish(n)  one block per tensor: ordered reduction of the partials into M^(n), the R x R
-//              solve with Gamma^(n) = Hadamard of the other Grams (Cholesky, or the eigen
-//              pseudoinverse when it fails), the Gram of the new A^(n)
-//   normalize  Eq. ALSnorm per tensor, with the column norms from the Gram diagonals
-//   eval       MTTKRPs of all modes in float64-accurate arithmetic, ||A Gamma - M||^2 per mode,
-//              g, the stopping and precision-switch decisions, all on the device
-// Unit sizes (elements per unit) come from a small autotuner that times candidate lists on the
-// batch itself.
+//              (tensor, block of 64 rows of the first mode, chunk of columns) and writes its
+//              partial sums, in the sweep's arithmetic, to a slot of its own, so each tensor's
+//              arithmetic is independent of what else is in the batch
+//   rows(n)    one warp per output row: ordered reduction of the row's partials into M^(n)(i,:)
+//              and the row of the R x R solve, A^(n)(i,:) = M^(n)(i,:) (Gamma^(n))^+
+//   tensor(n)  one block per tensor: the float64 Gram of the new A^(n), Eq. ALSnorm after the
+//              last mode (column norms from the Gram diagonals), and (Gamma^(n+1))^+ of the next
+//              mode (Gauss-Jordan, or the eigen pseudoinverse when Gamma is singular)
+//   eval       MTTKRPs of all modes in float64-accurate arithmetic, ||A Gamma - M||^2 per row
+//              and mode, g, the stopping and precision-switch decisions, all on the device
+// GB300's float64 pipe is narrow, so the float sweeps do no float64 arithmetic per column or per
+// row: they read float-pair copies of the factors and of Gamma^+ that the kernel keeps next to
+// the float64 ones, and sum in float (FP32) or float pairs (float64-accurate).  The Grams, the
+// inverses and the g evaluation stay float64.  Unit sizes (elements per unit) come from a small
+// autotuner that times candidate lists on the batch itself.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -33,7 +37,7 @@
 
 namespace cpmg {
 
-constexpr int kBR = 8;          // largest rank of the batched kernels (columns padded to 8)
+constexpr int kBR = 8;          // largest rank of the batched kernels (slots padded to 8)
 constexpr int kBModes = 4;      // largest order
 constexpr int kBRows = 64;      // first-mode rows per unit (two per lane)
 constexpr int kBThreads = 256;
@@ -47,17 +51,23 @@ enum { BS_RUNNING = -1 };
 struct BTen {
   const void* Z;
   double* A[kBModes];
+  float* Ah[kBModes];           // A as float pairs (hi, lo), same layout; kept when shadow != 0
+  float* Al[kBModes];
   double* gram;                 // kBModes x 8 x 8
   double* ginv;                 // 8 x 8: (Gamma^(n))^+ of the next mode to update
+  float* gih;                   // ginv as float pairs (8 x 8 each)
+  float* gil;
+  double* gam;                  // kBModes x 8 x 8: Gamma^(n) of every mode (g evaluation)
   double* rowres;               // per mode and row: ||A Gamma - M||^2, ||M||^2, <M, A> (g evaluation)
-  double* part[kBModes];        // partial sums of the MTTKRP of each mode
+  double* part[kBModes];        // partial sums of the MTTKRP of each mode, in the phase's arithmetic
   int64_t dims[kBModes];
   int nk[kBModes];              // partial slots per output row (mode > 0) or column chunks (mode 0)
   int N, R, zf64;
   int prec, gprec;              // sweep / evaluation arithmetic
+  int shadow;                   // 1: float sweeps (the float-pair copies are kept)
   int policy;                   // cpmg_precision of the request
   int active;
-  int init;                     // 1: ||Z||^2 and the Grams still to be computed
+  int init;                     // 1: ||Z||^2, the Grams and the copies still to be computed
   int status;
   int iters, max_iters;
   int stall;
@@ -101,39 +111,83 @@ template <> struct BT<BP_FP32> { using V = float; };
 template <> struct BT<BP_FP64> { using V = double; };
 template <> struct BT<BP_DF> { using V = df; };
 
-template <typename V> __device__ __forceinline__ V bconv(double x);
-template <> __device__ __forceinline__ float bconv<float>(double x) { return (float)x; }
-template <> __device__ __forceinline__ double bconv<double>(double x) { return x; }
-template <> __device__ __forceinline__ df bconv<df>(double x) { return df_from_double(x); }
-
 template <typename V> __device__ __forceinline__ V bzero();
 template <> __device__ __forceinline__ float bzero<float>() { return 0.f; }
 template <> __device__ __forceinline__ double bzero<double>() { return 0.0; }
 template <> __device__ __forceinline__ df bzero<df>() { return {0.f, 0.f}; }
+template <typename V> __device__ __forceinline__ V bone();
+template <> __device__ __forceinline__ float bone<float>() { return 1.f; }
+template <> __device__ __forceinline__ double bone<double>() { return 1.0; }
+template <> __device__ __forceinline__ df bone<df>() { return {1.f, 0.f}; }
 
 __device__ __forceinline__ void bfma(float& acc, float z, float w) { acc = __fmaf_rn(z, w, acc); }
 __device__ __forceinline__ void bfma(double& acc, float z, double w) { acc = __fma_rn((double)z, w, acc); }
 __device__ __forceinline__ void bfma(double& acc, double z, double w) { acc = __fma_rn(z, w, acc); }
 __device__ __forceinline__ void bfma(df& acc, float z, df w) { acc = df_add(acc, df_mul_f(z, w)); }
 
+__device__ __forceinline__ float badd(float a, float b) { return a + b; }
+__device__ __forceinline__ double badd(double a, double b) { return a + b; }
+__device__ __forceinline__ df badd(df a, df b) { return df_add(a, b); }
+
 __device__ __forceinline__ double bto_d(float x) { return (double)x; }
 __device__ __forceinline__ double bto_d(double x) { return x; }
 __device__ __forceinline__ double bto_d(df x) { return df_to_double(x); }
 
-// w *= a (a float64 factor entry) in the compute precision: float products for FP32, float
-// pairs for the float64-accurate path (GB300's float64 pipe is narrow; this runs per column)
-__device__ __forceinline__ void bwmul(float& w, double a) { w *= (float)a; }
-__device__ __forceinline__ void bwmul(double& w, double a) { w *= a; }
-__device__ __forceinline__ void bwmul(df& w, double a) { w = df_mul(w, df_from_double(a)); }
-template <typename V> __device__ __forceinline__ V bone();
-template <> __device__ __forceinline__ float bone<float>() { return 1.f; }
-template <> __device__ __forceinline__ double bone<double>() { return 1.0; }
-template <> __device__ __forceinline__ df bone<df>() { return {1.f, 0.f}; }
+__device__ __forceinline__ float bshfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double bshfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df bshfl_xor(df v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ float bshfl(float v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ double bshfl(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ df bshfl(df v, int l) {
+  return {__shfl_sync(0xffffffffu, v.hi, l), __shfl_sync(0xffffffffu, v.lo, l)};
+}
 
-// a * y in the compute precision, returned as float64 (the cross-lane sums run in float64)
-__device__ __forceinline__ double bmul_d(double a, float y) { return (double)((float)a * y); }
-__device__ __forceinline__ double bmul_d(double a, double y) { return a * y; }
-__device__ __forceinline__ double bmul_d(double a, df y) { return df_to_double(df_mul(df_from_double(a), y)); }
+// factor entry e of mode m in the arithmetic of V: the float copy (FP32), the float-pair copy
+// (float64-accurate), or the float64 array
+struct BFac {
+  const double* a;
+  const float* h;
+  const float* l;
+};
+__device__ __forceinline__ void fac_get(const BFac& f, size_t e, float& v) { v = f.h[e]; }
+__device__ __forceinline__ void fac_get(const BFac& f, size_t e, df& v) { v = {f.h[e], f.l[e]}; }
+__device__ __forceinline__ void fac_get(const BFac& f, size_t e, double& v) { v = f.a[e]; }
+__device__ __forceinline__ float bmul(float a, float b) { return a * b; }
+__device__ __forceinline__ double bmul(double a, double b) { return a * b; }
+__device__ __forceinline__ df bmul(df a, df b) { return df_mul(a, b); }
+
+// Sum of v[r] over the 32 lanes of the warp, scattered: returns the total of component
+// lane / (32 / RB).  log2(RB) halving exchanges, then a butterfly over the lanes holding the
+// same component; the order is fixed, so the result is reproducible.
+template <int RB, typename V>
+__device__ __forceinline__ V warp_rs(V (&v)[RB], int lane) {
+#pragma unroll
+  for (int h = RB / 2, s = 16; h >= 1; h >>= 1, s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const V keep = up ? v[h + j] : v[j];
+      const V give = up ? v[j] : v[h + j];
+      v[j] = badd(keep, bshfl_xor(give, s));
+    }
+  }
+  V x = v[0];
+#pragma unroll
+  for (int s = 16 / RB; s >= 1; s >>= 1) x = badd(x, bshfl_xor(x, s));
+  return x;
+}
+
+// A^(m)(e) <- x, with the float-pair copy when the tensor keeps one
+__device__ __forceinline__ void put_a(const BTen& T, int m, int64_t e, double x) {
+  T.A[m][e] = x;
+  if (T.shadow) {
+    const df d = df_from_double(x);
+    T.Ah[m][e] = d.hi;
+    T.Al[m][e] = d.lo;
+  }
+}
 
 // ------------------------------------------------------------------ grid barrier (bounded)
 __device__ __forceinline__ uint64_t bclock() {
@@ -173,105 +227,153 @@ __device__ bool grid_sync(unsigned* bar, int* err) {
 }
 
 // ------------------------------------------------------------------ MTTKRP unit (one warp)
-template <int P, typename TZ>
-__device__ void unit_run(const BTen& T, const BUnit& u, int lane, void* wsv, int64_t* wc) {
+// Rows r0..r0+63 of the first mode (two per lane) against 32 columns at a time: each lane forms
+// the Khatri-Rao row of one column (components r < RB) into shared memory, then every lane
+// accumulates its two tensor rows against the 32 rows, four columns' loads in flight at once.
+// Index arithmetic is 32-bit (batched tensors hold fewer than 2^32 elements).
+template <int P, typename TZ, int RB>
+__device__ void unit_run(const BTen& T, const BUnit& u, int lane, void* wsv, uint32_t* wc) {
   using V = typename BT<P>::V;
   V* ws = reinterpret_cast<V*>(wsv);
   const int N = T.N, R = T.R, n = u.mode;
-  const int64_t I0 = T.dims[0];
+  uint32_t dims[kBModes];
+  BFac fac[kBModes];
+#pragma unroll
+  for (int m = 0; m < kBModes; ++m) {
+    dims[m] = (uint32_t)T.dims[m];
+    fac[m] = {T.A[m], T.Ah[m], T.Al[m]};
+  }
+  const uint32_t I0 = dims[0];
   const TZ* Z = reinterpret_cast<const TZ*>(T.Z);
-  int64_t Lp = 1;
-  for (int m = 1; m < n; ++m) Lp *= T.dims[m];
-  const int64_t In = T.dims[n];
-  const int64_t r0 = (int64_t)u.rb * kBRows;
-  const int64_t rend = (r0 + kBRows < I0) ? r0 + kBRows : I0;
-  V acc[2][kBR];
+  uint32_t Lp = 1;
+#pragma unroll
+  for (int m = 1; m < kBModes; ++m)
+    if (m < n) Lp *= dims[m];
+  const uint32_t In = dims[n < kBModes ? n : 0];
+  const uint32_t r0 = (uint32_t)u.rb * kBRows;
+  const uint32_t rend = (r0 + kBRows < I0) ? r0 + kBRows : I0;
+  const uint32_t c1 = (uint32_t)u.c1, inx = (uint32_t)u.in_idx;
+  V acc[2][RB];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
-    for (int r = 0; r < kBR; ++r) acc[q][r] = bzero<V>();
-  for (int64_t jb = u.c0; jb < u.c1; jb += 32) {
-    const int cnt = (int)(u.c1 - jb < 32 ? u.c1 - jb : 32);
+    for (int r = 0; r < RB; ++r) acc[q][r] = bzero<V>();
+  const uint32_t i1a = r0 + lane, i1b = r0 + lane + 32;
+  const bool va = i1a < rend, vb = i1b < rend;
+  for (uint32_t jb = (uint32_t)u.c0; jb < c1; jb += 32) {
+    const int cnt = (int)(c1 - jb < 32 ? c1 - jb : 32);
     if (lane < cnt) {
-      const int64_t j = jb + lane;
-      const int64_t col = (n == 0) ? j : (j % Lp) + Lp * (u.in_idx + In * (j / Lp));
+      const uint32_t j = jb + lane;
+      const uint32_t col = (n == 0) ? j : (j % Lp) + Lp * (inx + In * (j / Lp));
       wc[lane] = col;
-      V w[kBR];
+      V w[RB];
 #pragma unroll
-      for (int r = 0; r < kBR; ++r) w[r] = bone<V>();
-      int64_t rem = col;
-      for (int m = 1; m < N; ++m) {
-        const int64_t Im = T.dims[m];
-        const int64_t im = rem % Im;
-        rem /= Im;
-        if (m != n) {
-          const double* Am = T.A[m];
+      for (int r = 0; r < RB; ++r) w[r] = bone<V>();
+      uint32_t rem = col;
 #pragma unroll
-          for (int r = 0; r < kBR; ++r)
-            if (r < R) bwmul(w[r], Am[im + Im * r]);
+      for (int m = 1; m < kBModes; ++m) {
+        if (m < N) {
+          const uint32_t Im = dims[m];
+          const uint32_t im = rem % Im;
+          rem /= Im;
+          if (m != n) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+              if (r < R) {
+                V a;
+                fac_get(fac[m], im + (size_t)Im * r, a);
+                w[r] = bmul(w[r], a);
+              }
+          }
         }
       }
 #pragma unroll
-      for (int r = 0; r < kBR; ++r) ws[lane * kBR + r] = (r < R) ? w[r] : bzero<V>();
+      for (int r = 0; r < RB; ++r) ws[lane * RB + r] = (r < R) ? w[r] : bzero<V>();
     }
     __syncwarp();
-    for (int jj = 0; jj < cnt; ++jj) {
-      const int64_t col = wc[jj];
-      V wr[kBR];
+    int jj = 0;
+    for (; jj + 4 <= cnt; jj += 4) {
+      TZ za[4], zb[4];
 #pragma unroll
-      for (int r = 0; r < kBR; ++r) wr[r] = ws[jj * kBR + r];
+      for (int c = 0; c < 4; ++c) {
+        const size_t base = (size_t)I0 * wc[jj + c];
+        za[c] = va ? Z[base + i1a] : TZ(0);
+        zb[c] = vb ? Z[base + i1b] : TZ(0);
+      }
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int64_t i1 = r0 + lane + 32 * q;
-        if (i1 < rend) {
-          const TZ z = Z[i1 + I0 * col];
+      for (int c = 0; c < 4; ++c) {
 #pragma unroll
-          for (int r = 0; r < kBR; ++r) bfma(acc[q][r], z, wr[r]);
+        for (int r = 0; r < RB; ++r) {
+          const V wr = ws[(jj + c) * RB + r];
+          bfma(acc[0][r], za[c], wr);
+          bfma(acc[1][r], zb[c], wr);
         }
+      }
+    }
+    for (; jj < cnt; ++jj) {
+      const size_t base = (size_t)I0 * wc[jj];
+      const TZ za = va ? Z[base + i1a] : TZ(0);
+      const TZ zb = vb ? Z[base + i1b] : TZ(0);
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const V wr = ws[jj * RB + r];
+        bfma(acc[0][r], za, wr);
+        bfma(acc[1][r], zb, wr);
       }
     }
     __syncwarp();
   }
   if (n == 0) {
-    double* Pp = T.part[0] + ((int64_t)u.k * I0) * kBR;
+    V* Pp = reinterpret_cast<V*>(T.part[0]) + (size_t)u.k * I0 * kBR;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const int64_t i1 = r0 + lane + 32 * q;
-      if (i1 < rend)
+      const uint32_t i1 = q ? i1b : i1a;
+      if (q ? vb : va)
 #pragma unroll
-        for (int r = 0; r < kBR; ++r) Pp[i1 * kBR + r] = bto_d(acc[q][r]);
+        for (int r = 0; r < RB; ++r) Pp[(size_t)i1 * kBR + r] = acc[q][r];
     }
   } else {
-    const double* A0 = T.A[0];
-    double t[kBR];
+    // contract the rows with A^(1): t[r] = sum_i1 A^(1)(i1, r) acc(i1, r), then over the warp
+    V t[RB];
 #pragma unroll
-    for (int r = 0; r < kBR; ++r) {
-      double s = 0.0;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int64_t i1 = r0 + lane + 32 * q;
-        if (i1 < rend && r < R) s += bmul_d(A0[i1 + I0 * r], acc[q][r]);
+    for (int r = 0; r < RB; ++r) {
+      V s = bzero<V>();
+      if (r < R) {
+        V a;
+        if (va) {
+          fac_get(fac[0], i1a + (size_t)I0 * r, a);
+          s = bmul(a, acc[0][r]);
+        }
+        if (vb) {
+          fac_get(fac[0], i1b + (size_t)I0 * r, a);
+          s = badd(s, bmul(a, acc[1][r]));
+        }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       t[r] = s;
     }
-    if (lane == 0) {
-      double* Pp = T.part[n] + ((int64_t)u.in_idx * T.nk[n] + u.k) * kBR;
-#pragma unroll
-      for (int r = 0; r < kBR; ++r) Pp[r] = t[r];
+    const V tot = warp_rs<RB>(t, lane);
+    constexpr int G = 32 / RB;
+    if (lane % G == 0) {
+      V* Pp = reinterpret_cast<V*>(T.part[n]) + ((size_t)u.in_idx * T.nk[n] + u.k) * kBR;
+      Pp[lane / G] = tot;
     }
   }
 }
 
 struct BSmem {
-  double ws[kBWarps][32 * kBR];   // Khatri-Rao rows of 32 columns (float / double / df)
-  int64_t wc[kBWarps][32];
+  double ws[kBWarps][32 * kBR];   // Khatri-Rao rows of 32 columns (float / double / float pairs)
+  uint32_t wc[kBWarps][32];
   double G[kBR * kBR], Pi[kBR * kBR], V[kBR * kBR], w[kBR];
   double red[3][kBThreads];
   double sc[kBModes][kBR];
   int fail;
 };
+
+template <int P, typename TZ>
+__device__ __forceinline__ void unit_dispatch(const BTen& T, const BUnit& u, int lane, void* ws, uint32_t* wc) {
+  if (T.R <= 4) unit_run<P, TZ, 4>(T, u, lane, ws, wc);
+  else unit_run<P, TZ, 8>(T, u, lane, ws, wc);
+}
 
 __device__ void phase_units(const BArgs& a, int n, bool eval, BSmem& sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -281,36 +383,11 @@ __device__ void phase_units(const BArgs& a, int n, bool eval, BSmem& sm) {
     const BTen& T = a.ten[u.t];
     if (!T.active) continue;
     const int p = eval ? T.gprec : T.prec;
-    if (T.zf64) unit_run<BP_FP64, double>(T, u, lane, sm.ws[warp], sm.wc[warp]);
-    else if (p == BP_FP32) unit_run<BP_FP32, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
-    else if (p == BP_DF) unit_run<BP_DF, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
-    else unit_run<BP_FP64, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+    if (T.zf64) unit_dispatch<BP_FP64, double>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+    else if (p == BP_FP32) unit_dispatch<BP_FP32, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+    else if (p == BP_DF) unit_dispatch<BP_DF, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+    else unit_dispatch<BP_FP64, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
   }
-}
-
-// M^(n) row i from the partials: lanes take terms lane, lane + 32, ..., then a fixed butterfly;
-// every lane ends with the whole row (fixed order, so reproducible)
-__device__ __forceinline__ void row_sum_warp(const BTen& T, int n, int64_t i, int lane, double* m) {
-#pragma unroll
-  for (int r = 0; r < kBR; ++r) m[r] = 0.0;
-  const int nk = T.nk[n];
-  if (n == 0) {
-    const int64_t I0 = T.dims[0];
-    for (int k = lane; k < nk; k += 32) {
-      const double* p = T.part[0] + ((int64_t)k * I0 + i) * kBR;
-#pragma unroll
-      for (int r = 0; r < kBR; ++r) m[r] += p[r];
-    }
-  } else {
-    const double* p = T.part[n] + (i * nk) * kBR;
-    for (int k = lane; k < nk; k += 32)
-#pragma unroll
-      for (int r = 0; r < kBR; ++r) m[r] += p[(int64_t)k * kBR + r];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int r = 0; r < kBR; ++r) m[r] += __shfl_xor_sync(0xffffffffu, m[r], o);
 }
 
 // deterministic block sum of one value per thread (thread 0 adds in thread order)
@@ -382,7 +459,8 @@ __device__ __noinline__ void bpinv(const double* G, double* Pi, double* V, doubl
     }
 }
 
-// T.ginv = (Gamma^(n))^+ with Gamma^(n) the Hadamard product of the other Grams (block-wide)
+// T.ginv = (Gamma^(n))^+ with Gamma^(n) the Hadamard product of the other Grams (block-wide),
+// plus its float-pair copy for the float sweeps
 __device__ void gamma_inverse(BTen& T, int n, BSmem& sm) {
   const int R = T.R, N = T.N;
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
@@ -398,8 +476,28 @@ __device__ void gamma_inverse(BTen& T, int n, BSmem& sm) {
   const double thresh = R * 2.220446049250313e-16 * (dmax > 0 ? dmax : 1.0);
   if (!gj_inverse(sm.Pi, R, thresh, &sm.fail) && threadIdx.x == 0) bpinv(sm.G, sm.Pi, sm.V, sm.w, R);
   __syncthreads();
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) T.ginv[(e / R) * kBR + (e % R)] = sm.Pi[e];
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int o = (e / R) * kBR + (e % R);
+    T.ginv[o] = sm.Pi[e];
+    if (T.shadow) {
+      const df d = df_from_double(sm.Pi[e]);
+      T.gih[o] = d.hi;
+      T.gil[o] = d.lo;
+    }
+  }
   __syncthreads();
+}
+
+// Gamma^(n) of every mode (for the residuals of the g evaluation; block-wide)
+__device__ void gamma_all(BTen& T) {
+  const int R = T.R, N = T.N;
+  for (int e = threadIdx.x; e < N * R * R; e += blockDim.x) {
+    const int n = e / (R * R), rc = e % (R * R), r = rc / R, c = rc % R;
+    double v = 1.0;
+    for (int m = 0; m < N; ++m)
+      if (m != n) v *= T.gram[m * kGramStride + r * kBR + c];
+    T.gam[n * kGramStride + r * kBR + c] = v;
+  }
 }
 
 // Eq. ALSnorm with the column norms taken from the Gram diagonals (block-wide)
@@ -422,7 +520,7 @@ __device__ void normalize_tensor(BTen& T, BSmem& sm) {
   __syncthreads();
   for (int m = 0; m < N; ++m) {
     const int Im = (int)T.dims[m];
-    for (int e = tid; e < Im * R; e += blockDim.x) T.A[m][e] *= sm.sc[m][e / Im];
+    for (int e = tid; e < Im * R; e += blockDim.x) put_a(T, m, e, T.A[m][e] * sm.sc[m][e / Im]);
     for (int e = tid; e < R * R; e += blockDim.x) {
       const int r = e / R, c = e % R;
       T.gram[m * kGramStride + r * kBR + c] *= sm.sc[m][r] * sm.sc[m][c];
@@ -433,64 +531,114 @@ __device__ void normalize_tensor(BTen& T, BSmem& sm) {
   __syncthreads();
 }
 
-// rows of mode n (or of every mode for the g evaluation): one warp per row.  update: the ALS
-// row A(i,:) = M(i,:) Gamma^+ (lane r forms component r).  !update: the row's contributions to
-// ||A Gamma - M||^2, ||M||^2 and <M, A>, stored per row for an ordered sum.
+// gi(k, r) times m_k: float-pair products for the float sweeps
+__device__ __forceinline__ df gi_mul(float m, const BTen& T, int o) { return df_mul_f(m, df{T.gih[o], T.gil[o]}); }
+__device__ __forceinline__ df gi_mul(df m, const BTen& T, int o) { return df_mul(m, df{T.gih[o], T.gil[o]}); }
+
+// Row i of mode n (one warp).  The lanes sum the row's partial slots lane, lane + 32, ... in
+// the phase's arithmetic and scatter-reduce them (lane holds component lane / (32 / RB)).
+// update: the ALS row A(i,:) = M(i,:) Gamma^+, lane r forming component r (float pairs for the
+// float sweeps, float64 for FP64).  !update: the row's contributions to ||A Gamma - M||^2,
+// ||M||^2 and <M, A> in float64, stored per row for an ordered sum.
+template <int P, int RB>
+__device__ void row_one(const BTen& T, int n, int64_t i, int lane, bool update) {
+  using V = typename BT<P>::V;
+  constexpr int G = 32 / RB;
+  const int R = T.R, N = T.N;
+  const int64_t In = T.dims[n];
+  const int nk = T.nk[n];
+  const V* base;
+  size_t stride;
+  if (n == 0) {
+    base = reinterpret_cast<const V*>(T.part[0]) + (size_t)i * kBR;
+    stride = (size_t)In * kBR;
+  } else {
+    base = reinterpret_cast<const V*>(T.part[n]) + (size_t)i * nk * kBR;
+    stride = kBR;
+  }
+  V m[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) m[r] = bzero<V>();
+  for (int k = lane; k < nk; k += 32) {
+    const V* p = base + (size_t)k * stride;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) m[r] = badd(m[r], p[r]);
+  }
+  const V mine = warp_rs<RB>(m, lane);
+  if (update) {
+    V mk[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) mk[k] = bshfl(mine, k * G);
+    if (lane < R) {
+      const int64_t e = i + In * lane;
+      if constexpr (P == BP_FP64) {
+        double x = 0.0;
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+          if (k < R) x = __fma_rn(mk[k], T.ginv[k * kBR + lane], x);
+        T.A[n][e] = x;
+      } else {
+        df x = {0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+          if (k < R) x = df_add(x, gi_mul(mk[k], T, k * kBR + lane));
+        T.A[n][e] = df_to_double(x);
+        T.Ah[n][e] = x.hi;
+        T.Al[n][e] = x.lo;
+      }
+    }
+  } else {
+    const V mv = bshfl(mine, (lane < RB ? lane : 0) * G);
+    double res = 0.0, mm = 0.0, zi = 0.0;
+    if (lane < R) {
+      const double* A = T.A[n];
+      const double* gm = T.gam + n * kGramStride;
+      double ag = 0.0;
+      for (int k = 0; k < R; ++k) ag = __fma_rn(A[i + In * k], gm[k * kBR + lane], ag);
+      const double mr = bto_d(mv);
+      const double d = ag - mr;
+      res = d * d;
+      mm = mr * mr;
+      zi = mr * A[i + In * lane];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      res += __shfl_xor_sync(0xffffffffu, res, o);
+      mm += __shfl_xor_sync(0xffffffffu, mm, o);
+      zi += __shfl_xor_sync(0xffffffffu, zi, o);
+    }
+    if (lane == 0) {
+      int64_t off = 0;
+      for (int q = 0; q < n; ++q) off += T.dims[q];
+      double* rr = T.rowres + 3 * (off + i);
+      rr[0] = res;
+      rr[1] = mm;
+      rr[2] = zi;
+    }
+  }
+  (void)N;
+}
+
+template <int P>
+__device__ __forceinline__ void row_dispatch(const BTen& T, int n, int64_t i, int lane, bool update) {
+  if (T.R <= 4) row_one<P, 4>(T, n, i, lane, update);
+  else row_one<P, 8>(T, n, i, lane, update);
+}
+
+// row items of mode n (or of every mode for the g evaluation): one warp per row
 __device__ void phase_rows(const BArgs& a, const BRow* items, int64_t nitems, bool update) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BRow rw = items[it];
     const BTen& T = a.ten[rw.t];
     if (!T.active) continue;
-    const int n = rw.mode, R = T.R, N = T.N;
-    const int64_t In = T.dims[n];
+    const int n = rw.mode;
     const int64_t i = rw.r0 + warp;
-    if (i >= In) continue;
-    double m[kBR];
-    row_sum_warp(T, n, i, lane, m);
-    double* A = T.A[n];
-    if (update) {
-      if (lane < R) {
-        double x = 0.0;
-#pragma unroll
-        for (int k = 0; k < kBR; ++k)
-          if (k < R) x = __fma_rn(m[k], T.ginv[k * kBR + lane], x);
-        A[i + In * lane] = x;
-      }
-    } else {
-      double res = 0.0, mm = 0.0, zi = 0.0;
-      if (lane < R) {
-        double ag = 0.0;
-        for (int k = 0; k < R; ++k) {
-          double gk = 1.0;
-          for (int q = 0; q < N; ++q)
-            if (q != n) gk *= T.gram[q * kGramStride + k * kBR + lane];
-          ag = __fma_rn(A[i + In * k], gk, ag);
-        }
-        double mr = 0.0;
-#pragma unroll
-        for (int r = 0; r < kBR; ++r)
-          if (r == lane) mr = m[r];
-        const double d = ag - mr;
-        res = d * d;
-        mm = mr * mr;
-        zi = mr * A[i + In * lane];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        res += __shfl_xor_sync(0xffffffffu, res, o);
-        mm += __shfl_xor_sync(0xffffffffu, mm, o);
-        zi += __shfl_xor_sync(0xffffffffu, zi, o);
-      }
-      if (lane == 0) {
-        int64_t off = 0;
-        for (int q = 0; q < n; ++q) off += T.dims[q];
-        double* rr = T.rowres + 3 * (off + i);
-        rr[0] = res;
-        rr[1] = mm;
-        rr[2] = zi;
-      }
-    }
+    if (i >= T.dims[n]) continue;
+    const int p = update ? T.prec : T.gprec;
+    if (T.zf64 || p == BP_FP64) row_dispatch<BP_FP64>(T, n, i, lane, update);
+    else if (p == BP_DF) row_dispatch<BP_DF>(T, n, i, lane, update);
+    else row_dispatch<BP_FP32>(T, n, i, lane, update);
   }
 }
 
@@ -583,6 +731,9 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BArgs a) {
   }
   if (a.eval && ok) {
     for (int n = 0; n < a.maxN; ++n) phase_units(a, n, a.eval == 1, sm);
+    if (a.eval == 1)
+      for (int t = blockIdx.x; t < a.nten; t += gridDim.x)
+        if (a.ten[t].active) gamma_all(a.ten[t]);
     ok = grid_sync(a.bar, a.err);
     if (a.eval == 1 && ok) {
       for (int n = 0; n < a.maxN; ++n) phase_rows(a, a.rows[n], a.nrows[n], false);
@@ -597,7 +748,8 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BArgs a) {
 }
 
 // ------------------------------------------------------------------ setup / final kernels
-// ||Z||^2, the Grams and Gamma^(1)^+ of every tensor still to initialize (block per tensor)
+// ||Z||^2, the Grams, the float-pair copies and Gamma^(1)^+ of every tensor still to initialize
+// (block per tensor)
 __global__ void __launch_bounds__(kBThreads) k_batch_init(BTen* ten, int nten) {
   __shared__ BSmem sm;
   __shared__ double buf[kBThreads];
@@ -628,7 +780,11 @@ __global__ void __launch_bounds__(kBThreads) k_batch_init(BTen* ten, int nten) {
       s = df_to_double(acc);
     }
     const double zz = bblock_sum(s, buf);
-    for (int m = 0; m < T.N; ++m) gram_rows(T.A[m], T.dims[m], T.R, T.gram + m * kGramStride, buf);
+    for (int m = 0; m < T.N; ++m) {
+      gram_rows(T.A[m], T.dims[m], T.R, T.gram + m * kGramStride, buf);
+      if (T.shadow)
+        for (int64_t e = threadIdx.x; e < T.dims[m] * T.R; e += blockDim.x) put_a(T, m, e, T.A[m][e]);
+    }
     gamma_inverse(T, 0, sm);
     if (threadIdx.x == 0) {
       T.znorm2 = zz;
@@ -746,11 +902,13 @@ static void plan_units(const std::vector<BItem>& items, std::vector<BUnit>* unit
   *part_total = off;
 }
 
-// per-tensor device state besides the factors: kBModes Grams, one Gamma^+, 3 doubles per row
+// per-tensor device state besides the factors: kBModes Grams, one Gamma^+ (float64 and float
+// pairs), kBModes Gammas, 3 doubles per row, and the float-pair copy of the factors (kBR pairs
+// per row)
 static size_t aux_doubles(const BItem& it) {
   int64_t rows = 0;
   for (int m = 0; m < it.N; ++m) rows += it.dims[m];
-  return (size_t)(kBModes + 1) * kGramStride + 3 * (size_t)rows;
+  return (size_t)(2 * kBModes + 2) * kGramStride + (3 + kBR) * (size_t)rows;
 }
 
 static size_t partial_doubles_of(const BItem& it) {
@@ -774,10 +932,22 @@ static BTen make_desc(const BItem& it) {
   }
   T.gram = it.gram;
   T.ginv = it.gram + kBModes * kGramStride;
-  T.rowres = T.ginv + kGramStride;
+  T.gam = T.ginv + kGramStride;
+  T.gih = reinterpret_cast<float*>(T.gam + kBModes * kGramStride);
+  T.gil = T.gih + kGramStride;
+  T.rowres = T.gam + (kBModes + 1) * kGramStride;
+  int64_t rows = 0;
+  for (int m = 0; m < it.N; ++m) rows += it.dims[m];
+  float* fb = reinterpret_cast<float*>(T.rowres + 3 * rows);
+  for (int m = 0; m < kBModes; ++m) {
+    T.Ah[m] = m < it.N ? fb : nullptr;
+    T.Al[m] = m < it.N ? fb + kBR * it.dims[m] : nullptr;
+    if (m < it.N) fb += 2 * kBR * it.dims[m];
+  }
   T.N = it.N;
   T.R = it.R;
   T.zf64 = it.zf64;
+  T.shadow = !(it.zf64 || it.o.precision == CPMG_PREC_FP64);
   if (it.has_state) return T;
   T.policy = it.o.precision;
   if (it.zf64 || it.o.precision == CPMG_PREC_FP64) {
@@ -1083,7 +1253,7 @@ static int check_item(const cpmg_tensor* Z, int R, double* const* A, const cpmg_
     if (Z->dims[m] < 1 || !A[m]) return CPMG_INVALID_ARG;
     P *= Z->dims[m];
   }
-  if (P >= (int64_t(1) << 40)) return CPMG_INVALID_ARG;
+  if (P >= (int64_t(1) << 32)) return CPMG_INVALID_ARG;  // 32-bit index arithmetic in the kernel
   std::memset(it, 0, sizeof(*it));
   it->Z = Z->data;
   it->zf64 = Z->dtype == CPMG_F64;
