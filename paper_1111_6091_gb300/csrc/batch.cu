@@ -123,7 +123,20 @@ template <> __device__ __forceinline__ df bone<df>() { return {1.f, 0.f}; }
 __device__ __forceinline__ void bfma(float& acc, float z, float w) { acc = __fmaf_rn(z, w, acc); }
 __device__ __forceinline__ void bfma(double& acc, float z, double w) { acc = __fma_rn((double)z, w, acc); }
 __device__ __forceinline__ void bfma(double& acc, double z, double w) { acc = __fma_rn(z, w, acc); }
-__device__ __forceinline__ void bfma(df& acc, float z, df w) { acc = df_add(acc, df_mul_f(z, w)); }
+// float pairs: the exact product z * w.hi (rounded part and error) plus z * w.lo; the rounded
+// parts are summed error-free into acc.hi (TwoSum) and every error term into acc.lo, which is
+// folded back by bnorm after each batch of at most 32 columns
+__device__ __forceinline__ void bfma(df& acc, float z, df w) {
+  const float p = __fmul_rn(z, w.hi);
+  float e = __fmaf_rn(z, w.hi, -p);
+  e = __fmaf_rn(z, w.lo, e);
+  const df s = df_two_sum(acc.hi, p);
+  acc.hi = s.hi;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, e));
+}
+__device__ __forceinline__ void bnorm(float&) {}
+__device__ __forceinline__ void bnorm(double&) {}
+__device__ __forceinline__ void bnorm(df& a) { a = df_two_sum(a.hi, a.lo); }
 
 __device__ __forceinline__ float badd(float a, float b) { return a + b; }
 __device__ __forceinline__ double badd(double a, double b) { return a + b; }
@@ -292,6 +305,27 @@ __device__ void unit_run(const BTen& T, const BUnit& u, int lane, void* wsv, uin
     }
     __syncwarp();
     int jj = 0;
+    if constexpr (sizeof(V) == 4 && sizeof(TZ) == 4) {
+      // FP32 sweeps are latency-bound: 16 loads in flight per lane (8 columns) per group
+      for (; jj + 8 <= cnt; jj += 8) {
+        float za[8], zb[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const size_t base = (size_t)I0 * wc[jj + c];
+          za[c] = va ? (float)Z[base + i1a] : 0.f;
+          zb[c] = vb ? (float)Z[base + i1b] : 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            const V wr = ws[(jj + c) * RB + r];
+            bfma(acc[0][r], za[c], wr);
+            bfma(acc[1][r], zb[c], wr);
+          }
+        }
+      }
+    }
     for (; jj + 4 <= cnt; jj += 4) {
       TZ za[4], zb[4];
 #pragma unroll
@@ -321,6 +355,10 @@ __device__ void unit_run(const BTen& T, const BUnit& u, int lane, void* wsv, uin
         bfma(acc[1][r], zb, wr);
       }
     }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int r = 0; r < RB; ++r) bnorm(acc[q][r]);
     __syncwarp();
   }
   if (n == 0) {
@@ -707,7 +745,7 @@ __device__ void check_tensor(BTen& T, int* nactive, BSmem& sm) {
   if (T.active) atomicAdd(nactive, 1);
 }
 
-__global__ void __launch_bounds__(kBThreads) k_batch(BArgs a) {
+__global__ void __launch_bounds__(kBThreads, 2) k_batch(BArgs a) {
   __shared__ BSmem sm;
   bool ok = true;
   for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
