@@ -49,6 +49,9 @@ template <> struct Ops<float> {
   __device__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
   __device__ static float mulz(float z, float a) { return z * a; }
   __device__ static float fmaz(float z, float a, float c) { return __fmaf_rn(z, a, c); }
+  __device__ static void acc(float& c, float z, float a) { c = __fmaf_rn(z, a, c); }
+  __device__ static void acc(float& c, float u, float w, int) { c = __fmaf_rn(u, w, c); }
+  __device__ static void norm(float&) {}
   __device__ static double to_d(float a) { return (double)a; }
 };
 template <> struct Ops<double> {
@@ -57,6 +60,9 @@ template <> struct Ops<double> {
   __device__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
   __device__ static double mulz(double z, double a) { return z * a; }
   __device__ static double fmaz(double z, double a, double c) { return __fma_rn(z, a, c); }
+  __device__ static void acc(double& c, double z, double a) { c = __fma_rn(z, a, c); }
+  __device__ static void acc(double& c, double u, double w, int) { c = __fma_rn(u, w, c); }
+  __device__ static void norm(double&) {}
   __device__ static double to_d(double a) { return a; }
 };
 template <> struct Ops<df> {
@@ -64,6 +70,27 @@ template <> struct Ops<df> {
   __device__ static df mul(df a, df b) { return df_mul(a, b); }
   __device__ static df fma(df a, df b, df c) { return df_add(c, df_mul(a, b)); }
   __device__ static df fmaz(float z, df a, df c) { return df_add(c, df_mul_f(z, a)); }
+  // Accumulation in the hot loops: the rounded product goes into c.hi by TwoSum, the product's
+  // rounding error and the TwoSum error into c.lo; norm folds c.lo back and runs after every
+  // few columns (a stage or an unrolled group), so c.lo never sums more than a handful of terms.
+  __device__ static void acc(df& c, float z, df a) {
+    const float p = __fmul_rn(z, a.hi);
+    float e = __fmaf_rn(z, a.hi, -p);
+    e = __fmaf_rn(z, a.lo, e);
+    const df s = df_two_sum(c.hi, p);
+    c.hi = s.hi;
+    c.lo = __fadd_rn(c.lo, __fadd_rn(s.lo, e));
+  }
+  __device__ static void acc(df& c, df u, df w, int) {
+    const float p = __fmul_rn(u.hi, w.hi);
+    float e = __fmaf_rn(u.hi, w.hi, -p);
+    e = __fmaf_rn(u.hi, w.lo, e);
+    e = __fmaf_rn(u.lo, w.hi, e);
+    const df s = df_two_sum(c.hi, p);
+    c.hi = s.hi;
+    c.lo = __fadd_rn(c.lo, __fadd_rn(s.lo, e));
+  }
+  __device__ static void norm(df& c) { c = df_two_sum(c.hi, c.lo); }
   __device__ static double to_d(df a) { return df_to_double(a); }
 };
 
@@ -291,7 +318,7 @@ __global__ void __launch_bounds__(max_threads(PREC, RP), 1) k_mttkrp_main(MainAr
 #pragma unroll
           for (int q = 0; q < VW; ++q)
 #pragma unroll
-            for (int r = 0; r < RP; ++r) accm[q][r] = Ops<V>::fmaz(zb[k][q], w[r], accm[q][r]);
+            for (int r = 0; r < RP; ++r) Ops<V>::acc(accm[q][r], zb[k][q], w[r]);
         } else {
           V uu[RP];
 #pragma unroll
@@ -302,11 +329,18 @@ __global__ void __launch_bounds__(max_threads(PREC, RP), 1) k_mttkrp_main(MainAr
 #pragma unroll
           for (int q = 1; q < QW; ++q)
 #pragma unroll
-            for (int r = 0; r < RP; ++r) uu[r] = Ops<V>::fmaz(zb[k][q], a1[q][r], uu[r]);
+            for (int r = 0; r < RP; ++r) Ops<V>::acc(uu[r], zb[k][q], a1[q][r]);
 #pragma unroll
-          for (int r = 0; r < RP; ++r) accm[0][r] = Ops<V>::fma(uu[r], w[r], accm[0][r]);
+          for (int r = 0; r < RP; ++r) {
+            Ops<V>::norm(uu[r]);
+            Ops<V>::acc(accm[0][r], uu[r], w[r], 0);
+          }
         }
       }
+#pragma unroll
+      for (int q = 0; q < QA; ++q)
+#pragma unroll
+        for (int r = 0; r < RP; ++r) Ops<V>::norm(accm[q][r]);
     }
   }
 
@@ -708,7 +742,7 @@ __global__ void __launch_bounds__(tma_threads(PREC, RP), 1) k_mttkrp_tma(TmaArgs
 #pragma unroll
                 for (int q = 0; q < VW; ++q)
 #pragma unroll
-                  for (int r = 0; r < RP; ++r) accm[q][r] = Ops<V>::fmaz(zb[q], w[r], accm[q][r]);
+                  for (int r = 0; r < RP; ++r) Ops<V>::acc(accm[q][r], zb[q], w[r]);
               } else {
                 V uu[RP];
 #pragma unroll
@@ -719,11 +753,20 @@ __global__ void __launch_bounds__(tma_threads(PREC, RP), 1) k_mttkrp_tma(TmaArgs
 #pragma unroll
                 for (int q = 1; q < QW; ++q)
 #pragma unroll
-                  for (int r = 0; r < RP; ++r) uu[r] = Ops<V>::fmaz(zb[q], a1[q][r], uu[r]);
+                  for (int r = 0; r < RP; ++r) Ops<V>::acc(uu[r], zb[q], a1[q][r]);
 #pragma unroll
-                for (int r = 0; r < RP; ++r) accm[0][r] = Ops<V>::fma(uu[r], w[r], accm[0][r]);
+                for (int r = 0; r < RP; ++r) {
+                  Ops<V>::norm(uu[r]);
+                  Ops<V>::acc(accm[0][r], uu[r], w[r], 0);
+                }
               }
             }
+          }
+          if constexpr (PREC == P_DF) {
+#pragma unroll
+            for (int q = 0; q < QA; ++q)
+#pragma unroll
+              for (int r = 0; r < RP; ++r) Ops<V>::norm(accm[q][r]);
           }
         }
         __syncwarp();
