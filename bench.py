@@ -524,18 +524,19 @@ def run_sweep_case(args):
 
 
 def run_batch_case(args):
-    """Small case for profiler captures: 64 tensors of the uneven batch workload, 16 MIXED
-    sweeps each in one batched solve (two launches of the persistent kernel)."""
+    """Profiler case: the 512-tensor batch workload, 8 MIXED sweeps of every tensor plus one g
+    evaluation.  Launches: the unit-size autotuner (5 candidates x (k_batch_init + 2 MTTKRP-only
+    k_batch)), then one k_batch of 8 sweeps + g, then k_batch_sort."""
     import torch
     from paper_1111_6091_gb300 import cpmg
-    probs = batch_problems(64)
+    probs = batch_problems(BATCH_COUNT)
     ctx = cpmg.Context(0)
     Zs = [cpmg.colmajor(p.Z) for p in probs]
     As = [[cpmg.colmajor(a) for a in p.A0] for p in probs]
-    st, res = cpmg.cpmg_batch_solve(ctx, Zs, As, precision=cpmg.PREC_MIXED, tol=0.0, max_als_iters=16,
+    st, res = cpmg.cpmg_batch_solve(ctx, Zs, As, precision=cpmg.PREC_MIXED, tol=0.0, max_als_iters=8,
                                     check_every=8)
     torch.cuda.synchronize()
-    print(json.dumps({"case": "batched 64 tensors", "sweeps": sum(r["iters_als"] for r in res)}))
+    print(json.dumps({"case": "batched %d tensors" % BATCH_COUNT, "sweeps": sum(r["iters_als"] for r in res)}))
     ctx.close()
 
 
@@ -561,7 +562,7 @@ def main():
     ap.add_argument("--case-prec", default="fp32", choices=["fp32", "df", "fp64"])
     ap.add_argument("--ttm-case", action="store_true", help="profiler case: one 400^3 restriction")
     ap.add_argument("--sweep-case", action="store_true", help="profiler case: 40 ALS sweeps at 100^3")
-    ap.add_argument("--batch-case", action="store_true", help="profiler case: a 64-tensor batched solve")
+    ap.add_argument("--batch-case", action="store_true", help="profiler case: one 8-sweep launch of the 512-tensor batch")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
