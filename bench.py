@@ -279,6 +279,7 @@ def run_gpu(args):
     del Z4, A4
     batched = run_batched(ctx, stream, args.batch_count) if args.batch_count > 0 else None
     served = run_served(args.serve_requests) if args.serve_requests > 0 else None
+    dense_ijk = run_paper_dense(ctx, stream) if not args.no_paper_dense else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -308,6 +309,7 @@ def run_gpu(args):
         "ttm_400cubed_tc": ttm4,
         "batched": batched,
         "served": served,
+        "paper_dense_ijk": dense_ijk,
         "cpu_baseline": cpu,
         "gpu_launches": int(launches),
         "gpu_launches_note": "kernel launches per step issued by libcpmg (graph replays count their kernels)",
@@ -434,6 +436,74 @@ def run_batched(ctx, stream, count=BATCH_COUNT):
     out["speedup_vs_loop"] = dt / out["mixed"]["seconds"]
     out["mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     return out
+
+
+def run_paper_dense(ctx, stream, s=100, R=3, reps=2):
+    """The paper's dense tensor z_ijk = (i^2+j^2+k^2)^(-1/2) (Section 6.3, Table tab:IJK test 6:
+    s = 100, R = 3), float64, to g < 1e-10 from uniform [0,1] starts: "Multilevel + FMG"
+    (mg_setup, mg_fmg with 100 coarsest ALS iterations, mg_fas_solve; levels down to 4) against
+    plain ALS (cp_als_sweep), both on the GPU in float64.  Wall time of the calls (each
+    synchronizes), best of `reps` after one warm-up."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg, synth
+    Z = synth.ijk_tensor(s)
+    rng = np.random.default_rng(0)
+    A0 = [rng.uniform(size=(s, R)) for _ in range(3)]
+    tfms = [[rng.uniform(size=(s, R)) for _ in range(3)] for _ in range(2)]
+    lv, I = 1, s
+    while (I + 1) // 2 >= 4:
+        I = (I + 1) // 2
+        lv += 1
+    Ac0 = [rng.uniform(size=(I, R)) for _ in range(3)]
+    kw = dict(precision=cpmg.PREC_FP64, tol=1e-10, coarsest=(I, I, I))
+    with torch.cuda.stream(stream):
+        Zd = cpmg.colmajor(Z)
+        A0d = [cpmg.colmajor(a) for a in A0]
+        T0d = [[cpmg.colmajor(a) for a in b] for b in tfms]
+        Acd = [cpmg.colmajor(a) for a in Ac0]
+    torch.cuda.synchronize()
+
+    def ml_fmg():
+        with torch.cuda.stream(stream):
+            A = [a.clone() for a in A0d]
+            T = [[a.clone() for a in b] for b in T0d]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            h, r1 = cpmg.mg_setup(ctx, Zd, A, T, **kw)
+            dims, _ = h.level_info(h.levels() - 1)
+            if tuple(int(dims[n]) for n in range(3)) != (I, I, I):
+                h.free()
+                raise RuntimeError("unexpected coarsest level %s" % (tuple(dims[:3]),))
+            rf = cpmg.mg_fmg(ctx, h, Zd, Acd, A, nu=100, **kw)
+            r2 = cpmg.mg_fas_solve(ctx, h, Zd, A, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h.free()
+        return dt, {"setup_cycles": r1["iters_setup"], "fmg_cycles": 1, "solve_cycles": r2["iters_solve"],
+                    "als_fallback_iters": r2["iters_als"], "g": r2["g"], "levels": r1["levels"],
+                    "status": r2["status"]}
+
+    def als():
+        with torch.cuda.stream(stream):
+            A = [a.clone() for a in A0d]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            r = cpmg.cp_als_sweep(ctx, Zd, A, 20000, precision=cpmg.PREC_FP64, tol=1e-10, check_every=-1)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, {"iters": r["iters_als"], "g": r["g"], "status": r["status"]}
+
+    best = {}
+    for name, fn in (("ml_fmg", ml_fmg), ("als", als)):
+        fn()
+        runs = [fn() for _ in range(reps)]
+        dt, info = min(runs, key=lambda x: x[0])
+        best[name] = dict(seconds=dt, **info)
+    return {"tensor": "z_ijk = (i^2+j^2+k^2)^(-1/2)", "s": s, "R": R, "tol": 1e-10, "precision": "fp64",
+            "levels": lv, **best, "speedup": best["als"]["seconds"] / best["ml_fmg"]["seconds"],
+            "paper_matlab_s": {"als": 80.2, "ml_fmg": 8.1, "note": "Table tab:IJK test 6, MATLAB on a 2.5 GHz "
+                                                                  "Core 2 Duo; context only"}}
 
 
 SERVE_RATE, SERVE_LARGE_FRAC = 2000.0, 0.05
@@ -568,6 +638,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-paper-dense", action="store_true", help="skip the paper's dense-tensor comparison")
+    ap.add_argument("--paper-dense", action="store_true", help="run only the paper's dense-tensor comparison")
     ap.add_argument("--solve-only", action="store_true", help="profiler case: the timed solves only")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT, help="batched workload size (0: skip)")
     ap.add_argument("--serve-requests", type=int, default=1000,
@@ -584,6 +656,13 @@ def main():
         run_sweep_case(args)
     elif args.batch_case:
         run_batch_case(args)
+    elif args.paper_dense:
+        import torch
+        from paper_1111_6091_gb300 import cpmg
+        stream = torch.cuda.Stream()
+        ctx = cpmg.Context(0, stream=stream.cuda_stream)
+        print(json.dumps(run_paper_dense(ctx, stream)), flush=True)
+        ctx.close()
     elif args.impl == "reference":
         run_reference(args)
     else:

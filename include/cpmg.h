@@ -209,6 +209,20 @@ int mg_setup(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A_boot,
  * stagnation.  A: in/out factors.  Z must be the tensor the hierarchy was built from. */
 int mg_fas_solve(cpmg_ctx* ctx, cpmg_hier* hier, const cpmg_tensor* Z, double* const* A,
                  const cpmg_opts* opts, cpmg_result* result);
+/* One FMG-CP-FAS cycle (Section 5.4 Algorithm 3) on a hierarchy from mg_setup, as the
+ * "Multilevel + FMG" variant of Section 6.1 uses it between the setup and solve phases: nu ALS
+ * iterations (normalized, components sorted at the end) on the coarsest level from A_coarsest,
+ * then on each finer level the interpolated factors (P-hat times the coarser level's) and one
+ * CP-FAS V-cycle with F = 0 topped at that level.  The hierarchy's operators are then rebuilt
+ * around the new finest-level factors by one down-sweep of CP-AMG-mult (boot factors frozen, the
+ * stored TFMs relaxed and updated), so mg_fas_solve can continue from A.
+ * A_coarsest: N float64 column-major arrays of the coarsest level's sizes (cpmg_hier_level_info
+ * of level cpmg_hier_levels - 1) x R, the coarsest-level start, read only.  A: N float64 I_n x R
+ * column-major arrays, out: the finest-level factors.  Both in Z->mem memory, owned by the
+ * caller.  nu >= 0 (the paper's experiments use 100).  result: f and g of A, levels.
+ * Errors: INVALID_ARG (null pointers, nu < 0, Z not the hierarchy's tensor), CUDA_ERROR. */
+int mg_fmg(cpmg_ctx* ctx, cpmg_hier* hier, const cpmg_tensor* Z, double* const* A_coarsest, double* const* A,
+           int nu, const cpmg_opts* opts, cpmg_result* result);
 void cpmg_hier_free(cpmg_hier* hier);
 int cpmg_hier_levels(const cpmg_hier* hier);
 /* Copy level `level`'s tensor dims (and, if Y != NULL, the device tensor itself, in the

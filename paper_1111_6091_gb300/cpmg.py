@@ -79,6 +79,8 @@ _SIGS = {
                            C.POINTER(C.c_void_p), C.POINTER(cpmg_result)]),
     "mg_fas_solve": (C.c_int, [_P, _P, C.POINTER(cpmg_tensor), _PP, C.POINTER(cpmg_opts),
                                C.POINTER(cpmg_result)]),
+    "mg_fmg": (C.c_int, [_P, _P, C.POINTER(cpmg_tensor), _PP, _PP, C.c_int, C.POINTER(cpmg_opts),
+                         C.POINTER(cpmg_result)]),
     "cpmg_hier_free": (None, [_P]),
     "cpmg_hier_levels": (C.c_int, [_P]),
     "cpmg_hier_level_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), _P, _PP]),
@@ -409,6 +411,17 @@ def mg_fas_solve(ctx, hier, Z, A, opts=None, **kw):
     d = tensor_desc(Z)
     s = lib().mg_fas_solve(ctx.h, hier.h, C.byref(d), _ptrs(A), C.byref(o), C.byref(r))
     _check(s, "mg_fas_solve", allow=(OK, NOT_CONVERGED))
+    return result_dict(r)
+
+
+def mg_fmg(ctx, hier, Z, A_coarsest, A, nu=100, opts=None, **kw):
+    """One FMG-CP-FAS cycle (Algorithm 3) from the coarsest-level start A_coarsest, then the
+    down-sweep rebuild of the hierarchy's operators; the finest-level factors go to A."""
+    o = opts or make_opts(**kw)
+    r = cpmg_result()
+    d = tensor_desc(Z)
+    s = lib().mg_fmg(ctx.h, hier.h, C.byref(d), _ptrs(A_coarsest), _ptrs(A), int(nu), C.byref(o), C.byref(r))
+    _check(s, "mg_fmg")
     return result_dict(r)
 
 

@@ -934,6 +934,32 @@ static int check_opts(const cpmg_opts* o) {
   return CPMG_OK;
 }
 
+// ============================================================================ Algorithm 3
+// FMG-CP-FAS: nu ALS iterations (normalized, sorted at the end) on the coarsest level from the
+// level's current factors, then for each finer level: prolongate by P-hat (the transpose of
+// R-hat; identity for modes not coarsened) and one CP-FAS cycle with F = 0 topped at that level.
+// Leaves the finest-level result in h->L[0].A.
+static int fmg_cycle(Solver& S, cpmg_hier* h, int nu) {
+  const int Lc = (int)h->L.size() - 1;
+  CPMG_TRY(relax_als(S, h->L[Lc], Lc, h->L[Lc].A, nu, true));
+  for (int lvl = Lc - 1; lvl >= 0; --lvl) {
+    Level& L = h->L[lvl];
+    const Level& C = h->L[lvl + 1];
+    for (int n = 0; n < L.s.N; ++n) {
+      if (L.co[n])
+        CPMG_TRY(launch_dgemm_small(true, L.s.dims[n], h->R, L.cd[n], 1.0, L.Rhat[n], L.cd[n], C.A.A[n],
+                                    L.cd[n], 0.0, L.A.A[n], L.s.dims[n], S.st));
+      else
+        CPMG_TRY(launch_copy_d(L.A.A[n], C.A.A[n], L.s.dims[n] * h->R, S.st));
+      S.c->launches += 1;
+    }
+    CPMG_TRY(launch_grams(L.A, all_modes(L.s.N), S.st));
+    S.c->launches += 1;
+    CPMG_TRY(cp_fas(S, h, lvl, false, lvl));
+  }
+  return CPMG_OK;
+}
+
 // ============================================================================ C ABI
 extern "C" {
 
@@ -1416,6 +1442,52 @@ int mg_fas_solve(cpmg_ctx* c, cpmg_hier* h, const cpmg_tensor* Z, double* const*
     res->iters_solve = solve;
     res->iters_als = als_it;
     res->restarted = restarted;
+    res->levels = (int)h->L.size();
+    res->refine_sweeps = S.refine_sweeps;
+    res->status = st;
+    res->seconds = now_s() - t0;
+  }
+  L0.Z = nullptr;
+  dfree(c, zv.own);
+  c->prof_Z = nullptr;
+  return st;
+}
+
+int mg_fmg(cpmg_ctx* c, cpmg_hier* h, const cpmg_tensor* Z, double* const* A_coarsest, double* const* A, int nu,
+           const cpmg_opts* opts, cpmg_result* res) {
+  cudaGetLastError();  // an error left pending by the caller is not this call's
+  const double t0 = now_s();
+  if (!c || !h || !A || !A_coarsest || nu < 0) return CPMG_INVALID_ARG;
+  CPMG_TRY(check_tensor(Z));
+  CPMG_TRY(check_opts(opts));
+  if (Z->N != h->N) return CPMG_INVALID_ARG;
+  for (int n = 0; n < Z->N; ++n)
+    if (Z->dims[n] != h->L[0].s.dims[n] || Z->dtype != h->L[0].dtype) return CPMG_INVALID_ARG;
+  Solver S = make_solver(c, opts);
+  S.sortbuf = h->sortbuf;
+  ZView zv;
+  int st = resolve_tensor(c, Z, &zv);
+  Level& L0 = h->L[0];
+  L0.Z = zv.dev;
+  c->prof_Z = L0.Z;
+  if (st == CPMG_OK) st = factors_in(c, Z->mem, A_coarsest, h->L.back().A);
+  if (st == CPMG_OK) st = tensor_norm(S, L0, L0.A, &S.znorm);
+  S.gc = &h->graphs;
+  S.z0 = L0.Z;
+  if (st == CPMG_OK) st = hier_preplan(c, h);
+  if (st == CPMG_OK) st = fmg_cycle(S, h, nu);
+  // the operators are rebuilt around the new factors by a down-sweep (boot factors frozen)
+  if (st == CPMG_OK) st = amg_mult(S, h, 0, false, false, false);
+  double g = -1, fv = 0;
+  if (st == CPMG_OK) st = eval_g(S, L0, L0.A, &g, nullptr);
+  if (st == CPMG_OK) st = eval_f(S, L0, L0.A, &fv, nullptr);
+  if (st == CPMG_OK) st = factors_out(c, Z->mem, L0.A, A);
+  if (st == CPMG_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = CPMG_CUDA_ERROR;
+  if (res) {
+    std::memset(res, 0, sizeof(*res));
+    res->f = fv;
+    res->g = g;
+    res->iters_setup = 1;
     res->levels = (int)h->L.size();
     res->refine_sweeps = S.refine_sweeps;
     res->status = st;

@@ -203,3 +203,49 @@ def test_restriction_on_tensor_cores_keeps_the_fixed_point(cpmg_ctx):
     assert align.factor_error(got[0], got[1]) <= 1e-6
     if ref.converged:
         assert align.factor_error(ref.A, got[1]) <= 1e-6
+
+
+def test_multilevel_fmg_on_the_papers_dense_tensor(cpmg_ctx):
+    """'Multilevel + FMG' (Section 6.1) on the paper's dense tensor z_ijk = (i^2+j^2+k^2)^(-1/2)
+    (Section 6.3), s = 50, R = 3, float64, as three calls: mg_setup, mg_fmg (Algorithm 3 plus the
+    down-sweep rebuild), mg_fas_solve.  Each stage is compared with the oracle's from identical
+    inputs (uniform [0,1] starts as in the paper), and the multilevel cycle count is far below the
+    ALS iteration count (the gap of Table tab:IJK)."""
+    from paper_1111_6091_gb300 import cpmg
+    s, R = 50, 3
+    Z = synth.ijk_tensor(s)
+    rng = np.random.default_rng(0)
+    A0 = [rng.uniform(size=(s, R)) for _ in range(3)]
+    tfms = [[rng.uniform(size=(s, R)) for _ in range(3)] for _ in range(2)]
+    Ac0 = [rng.uniform(size=(4, R)) for _ in range(3)]
+    o = MG.Options(coarsest=(4, 4, 4), tol=1e-10)
+    kw = dict(precision=cpmg.PREC_FP64, tol=1e-10, coarsest=(4, 4, 4))
+    # oracle, stage by stage (the body of multilevel_fmg)
+    su = MG.mg_setup(Z, A0, tfms, o)
+    A_fmg = MG.fmg_cp_fas(su.levels, Ac0, 100, o)
+    levels, tf2 = MG.down_sweep(Z, A_fmg, su.tfms, o)
+    ref = MG.mg_fas_solve(Z, levels, A_fmg, tf2, o, cycles_done=su.setup_cycles + 1)
+    assert ref.converged and len(levels) == 5
+    # GPU
+    Zd = cpmg.colmajor(Z)
+    A = dev(cpmg, A0)
+    tf = [dev(cpmg, b) for b in tfms]
+    h, r1 = cpmg.mg_setup(cpmg_ctx, Zd, A, tf, **kw)
+    try:
+        assert r1["levels"] == 5 and r1["iters_setup"] == su.setup_cycles
+        dims, _ = h.level_info(4)
+        assert tuple(int(dims[n]) for n in range(3)) == (4, 4, 4)
+        rf = cpmg.mg_fmg(cpmg_ctx, h, Zd, dev(cpmg, Ac0), A, nu=100, **kw)
+        got_fmg = host(cpmg, A)
+        for a, b in zip(got_fmg, A_fmg):
+            assert np.max(np.abs(a - b)) <= 1e-8 * np.max(np.abs(b))
+        assert np.isclose(rf["g"], T.g_value(Z, A_fmg), rtol=1e-6)
+        r2 = cpmg.mg_fas_solve(cpmg_ctx, h, Zd, A, **kw)
+    finally:
+        h.free()
+    got = host(cpmg, A)
+    assert r2["status"] == cpmg.OK and T.g_value(Z, got) < 1e-10
+    assert r2["iters_solve"] == ref.solve_cycles
+    assert align.factor_error(ref.A, got) <= 1e-7
+    _, it_als = ALS.als(Z, A0, 10000, tol=1e-10, g_fn=T.g_value)
+    assert (r1["iters_setup"] + 1 + r2["iters_solve"]) * 20 < it_als
