@@ -84,7 +84,7 @@ def blas_threads():
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return
     p = problem()
@@ -152,13 +152,36 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def rank_env():
+    """(world size, rank, local rank) from the launcher's environment (1, 0, 0 without one)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def ranks_barrier():
+    """Barrier over the process group, if one is running (the timed region's edges)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def max_over_ranks(x, device="cpu"):
+    """The largest per-rank value over the process group: the job's step time is its slowest
+    replica's.  Without a process group, x itself."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args):
     import torch
     from paper_1111_6091_gb300 import cpmg
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -191,8 +214,7 @@ def run_gpu(args):
             reset()
             step()
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        ranks_barrier()
         clocks = Clocks()
         clocks.start()
         launches0 = ctx.launches()
@@ -207,6 +229,7 @@ def run_gpu(args):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
+        ranks_barrier()
         launches = (ctx.launches() - launches0) // max(args.steps, 1)
         clk = clocks.stop()
         # One more identical step with per-launch CUDA events on the finest-level MTTKRP main
@@ -219,11 +242,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         prof = [ctx.profile_read(k) for k in range(3)]
         ctx.profile(False)
-    t_step = max(ms_i for ms_i in [statistics.mean(ms)])
-    if world > 1:
-        t = torch.tensor([t_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(statistics.mean(ms), device="cuda")
 
     if args.solve_only:
         if rank == 0:
