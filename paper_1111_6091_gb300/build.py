@@ -2,7 +2,7 @@
 
 Each ``csrc/*.cu`` translation unit compiles in parallel to ``_build/<name>.o``;
 the objects link into ``paper_1111_6091_gb300/libcpmg.so`` (CUDA runtime linked
-statically, so the library needs only the driver at run time).  Objects are
+statically, so the library needs only the CUDA driver at run time).  Objects are
 rebuilt when their source or any header is newer.
 """
 from __future__ import annotations

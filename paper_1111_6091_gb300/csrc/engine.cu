@@ -1,8 +1,8 @@
 // Host engine of libcpmg: context and device memory, MTTKRP plans, the relaxations
 // (ALS of Section 3, BNGS of Section 5.2), the multigrid hierarchy, CP-AMG-mult
-// (Algorithm 1), CP-FAS (Algorithm 2), the setup/solve driver of Section 6.1 and the
-// C ABI declared in include/cpmg.h.  All arithmetic runs in the kernels; the host only
-// orders launches and reads back scalars (g, f) to take the driver's decisions.
+// (Algorithm 1), CP-FAS (Algorithm 2), FMG-CP-FAS (Algorithm 3), the setup/solve control of
+// Section 6.1 and the C ABI declared in include/cpmg.h.  All arithmetic runs in the kernels;
+// the host only orders launches and reads back scalars (g, f) for the control decisions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
