@@ -101,7 +101,7 @@ typedef struct {
   int als_fallback;                  /* 1: plain ALS after a second solve-phase stagnation    */
                                      /*    (an addition; the paper stops after one rebuild)   */
   double mixed_switch;               /* MIXED: switch to float64-accurate sweeps when
-                                        g < mixed_switch * (FP32 floor estimate); <= 0: 64     */
+                                        g < mixed_switch * (FP32 floor estimate); <= 0: 4      */
   int check_every;                   /* cp_als_sweep: exact g every k sweeps (0 = never; < 0 =
                                         adaptive interval, at most 32, from the observed rate)  */
   int use_graphs;                    /* 1: capture sweeps / cycles as CUDA graphs and replay

@@ -1000,7 +1000,7 @@ static BTen make_desc(const BItem& it) {
   T.status = BS_RUNNING;
   T.max_iters = it.o.max_als_iters;
   T.tol = it.o.tol;
-  T.mixed_switch = it.o.mixed_switch > 0 ? it.o.mixed_switch : 64.0;
+  T.mixed_switch = it.o.mixed_switch > 0 ? it.o.mixed_switch : 4.0;
   T.g = -1.0;
   T.g_best = -1.0;
   return T;

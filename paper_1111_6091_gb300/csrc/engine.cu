@@ -591,7 +591,7 @@ static int eval_g(Solver& S, const Level& L, FactorSet& f, double* g, double* mn
 // MTTKRP seen through Eq. gradConv), or after 20 checks without a new smallest g.
 static void maybe_switch(Solver& S, double g, double mnorm, double /*g_prev*/) {
   if (S.policy != CPMG_PREC_MIXED || S.refined) return;
-  const double K = S.o.mixed_switch > 0 ? S.o.mixed_switch : 64.0;
+  const double K = S.o.mixed_switch > 0 ? S.o.mixed_switch : 4.0;
   const double floor_est = K * 5.960464477539063e-08 * mnorm / S.znorm;
   if (S.g_best < 0 || g < S.g_best) {
     S.g_best = g;
@@ -981,7 +981,7 @@ void cpmg_opts_default(cpmg_opts* o) {
   o->stag_eps = 0.1;
   o->gs_sweeps = 10;
   o->als_fallback = 0;
-  o->mixed_switch = 64.0;
+  o->mixed_switch = 4.0;
   o->check_every = 1;
   o->use_graphs = 1;
   o->ttm_tensor_cores = 1;
