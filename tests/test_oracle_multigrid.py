@@ -229,3 +229,51 @@ def test_last_mode_gradient_is_zero_after_als_so_weights_cap():
     U = np.hstack([b[2] for b in blocks])
     w = np.array([MG.block_weight(p.Z, b, 2) for b in blocks]).repeat(3)
     assert np.allclose(MG.interpolation(U, w, 8), MG.interpolation(U, np.ones(6), 8), rtol=1e-12)
+
+
+def _nested_exact_hierarchy(dims, R, seed):
+    """Three levels with hand-built interpolation operators and a tensor whose factors lie in
+    the range of the whole chain: A_0 = P-hat_0 A_1, A_1 = P-hat_1 A_2.  Since R-hat P-hat = I,
+    every level's tensor is exactly [[A_l]]."""
+    rng = np.random.default_rng(seed)
+    ops, sizes = [], [tuple(dims)]
+    for _ in range(2):
+        lv = []
+        for I in sizes[-1]:
+            P = MG.interpolation(rng.standard_normal((I, 2 * R)), np.ones(2 * R), I)
+            lv.append((P,) + MG.transform(P))
+        ops.append(lv)
+        sizes.append(tuple(MG.coarse_size(I) for I in sizes[-1]))
+    A2 = [rng.standard_normal((I, R)) for I in sizes[2]]
+    A1 = [o[1] @ a for o, a in zip(ops[1], A2)]
+    A0 = [o[1] @ a for o, a in zip(ops[0], A1)]
+    Z0 = T.cp_full(A0)
+    Z1 = MG.coarse_tensor(Z0, [o[2] for o in ops[0]], [True] * 3)
+    Z2 = MG.coarse_tensor(Z1, [o[2] for o in ops[1]], [True] * 3)
+    levels = [MG.Level(Z, [True] * 3, [o[0] for o in op], [o[1] for o in op], [o[2] for o in op])
+              for Z, op in ((Z0, ops[0]), (Z1, ops[1]))]
+    levels.append(MG.Level(Z2, [False] * 3, [None] * 3, [None] * 3, [None] * 3))
+    return levels, (A0, A1, A2), rng
+
+
+def test_fmg_recovers_factors_in_the_range_of_the_interpolation_chain():
+    """Algorithm 3 (nested iteration): when the fine factors lie in the range of P-hat_0 P-hat_1,
+    every coarse tensor is exactly the restricted decomposition, so the coarsest ALS solve followed
+    by prolongation (P-hat, not P) and one CP-FAS cycle per level returns the exact fine
+    decomposition."""
+    levels, (A0, A1, A2), rng = _nested_exact_hierarchy((13, 11, 9), 2, 21)
+    assert np.allclose(levels[1].Z, T.cp_full(A1), atol=1e-12 * np.max(np.abs(levels[1].Z)))
+    assert np.allclose(levels[2].Z, T.cp_full(A2), atol=1e-12 * np.max(np.abs(levels[2].Z)))
+    opts = MG.Options(tol=1e-10)
+    # exact coarsest start, no coarse iterations: the prolongated factors are already exact
+    A = MG.fmg_cp_fas(levels, A2, 0, opts)
+    assert T.g_value(levels[0].Z, A) < 1e-12
+    assert align.factor_error(A0, A) < 1e-10
+    # perturbed coarsest start: the coarsest ALS converges, the rest follows
+    start = [a + 0.3 * np.std(a) * rng.standard_normal(a.shape) for a in A2]
+    A = MG.fmg_cp_fas(levels, start, 300, opts)
+    assert T.g_value(levels[0].Z, A) < 1e-9
+    assert align.factor_error(A0, A) < 1e-7
+    # prolongating with P instead of P-hat (a plausible slip) would not be exact
+    bad = [L.P[n] @ a for L in levels[:1] for n, a in enumerate(MG.fmg_cp_fas(levels[1:], A2, 0, opts))]
+    assert T.g_value(levels[0].Z, bad) > 1e-3
