@@ -312,7 +312,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": t_step * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": False,
-        "scaling": "weak" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
         "config": config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
