@@ -302,6 +302,8 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
+        if batched is not None:
+            batched["cpu_oracle_sample"] = oracle_batch_sample()
         dt, r = oracle_solve(p)
         cpu = {"value": dt, "unit": "s", "cores": blas_threads(), "kind": "oracle",
                "sample": "one full solve of the workload by the FP64 NumPy oracle (same solver and start)",
@@ -402,6 +404,22 @@ def batch_problems(count, seed=0):
     return [synth.make_problem(sp["dims"], sp["R"], congruence=sp["congruence"], eta_homo=0.01,
                                dtype=np.float32, seed=sp["seed"], n_t=0)
             for sp in synth.batch_specs(count, seed)]
+
+
+def oracle_batch_sample(count=32, sweeps=5):
+    """The FP64 oracle's ALS on a bounded sample of the batch workload (its first `count`
+    tensors, `sweeps` sweeps each), as tensor-sweeps per second on the host cores."""
+    from oracle import als as ALS
+    probs = batch_problems(count)
+    t = time.perf_counter()
+    for p in probs:
+        A = p.A0
+        Z64 = p.Z.astype(np.float64)
+        for _ in range(sweeps):
+            A = ALS.als_sweep(Z64, A)
+    dt = time.perf_counter() - t
+    return {"value": count * sweeps / dt, "unit": "tensor-sweeps/s", "cores": blas_threads(), "kind": "oracle",
+            "sample": f"FP64 NumPy ALS, {sweeps} sweeps of each of the first {count} tensors of the batch"}
 
 
 def run_batched(ctx, stream, count=BATCH_COUNT):
