@@ -38,6 +38,9 @@ def test_opts_default_is_the_paper_table(lib):
     assert (o.nu1, o.nu2, o.nuc) == (1, 1, 50)
     assert o.gs_sweeps == 10 and o.max_cycles == 500 and o.max_als_iters == 10000
     assert o.max_setup_cycles == 5 and abs(o.stag_eps - 0.1) < 1e-15 and o.tol == 1e-10
+    # additions that are not in the paper's table: MIXED policy with switch factor 4, no ALS
+    # fallback unless asked for
+    assert o.precision == cpmg.PREC_MIXED and o.mixed_switch == 4.0 and o.als_fallback == 0
 
 
 def test_status_strings(lib):
@@ -56,6 +59,14 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.mg_fas_solve(None, None, None, None, C.byref(o), C.byref(r)) == cpmg.INVALID_ARG
     assert lib.cpmg_hier_levels(None) == 0
     assert lib.cpmg_bytes_in_use(None) == 0
+    assert lib.mg_fmg(None, None, None, None, None, 100, C.byref(o), C.byref(r)) == cpmg.INVALID_ARG
+    assert lib.cpmg_batch_solve(None, 1, None, None, None, C.byref(o), C.byref(r)) == cpmg.INVALID_ARG
+    t = C.c_uint64()
+    assert lib.cpmg_server_submit(None, None, 2, None, C.byref(o), C.byref(t)) == cpmg.INVALID_ARG
+    assert lib.cpmg_server_poll(None, 1, C.byref(r)) == cpmg.INVALID_ARG
+    assert lib.cpmg_server_wait(None, 0.0) == cpmg.INVALID_ARG
+    assert lib.cpmg_server_config(None, 0, 0, 0, 0) == cpmg.INVALID_ARG
+    assert lib.cpmg_server_stats(None, None, None, None, None) == cpmg.INVALID_ARG
 
 
 def test_struct_layout_matches_header(lib):
