@@ -255,6 +255,19 @@ int cpmg_decompose(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A,
 int cpmg_batch_solve(cpmg_ctx* ctx, int count, const cpmg_tensor* Z, const int* R, double* const* const* A,
                      const cpmg_opts* opts, cpmg_result* results);
 
+/* Host-only inspection of the batched form's work split (no GPU needed): the MTTKRP work units
+ * of mode `mode` of one tensor (order N, sizes dims, rank R) at unit size unit_elements.  A unit
+ * covers first-mode rows 64*rb .. 64*rb+63 (clipped) and columns c0..c1-1 of the mode's column
+ * range: all columns of the mode-1 unfolding for mode 0; for mode n > 0 the columns that share
+ * i_n = in_idx.  It writes its partial sums to slot k (per column chunk for mode 0; per i_n and
+ * (chunk, row block) otherwise).  units: max_units x 5 int64 (rb, k, c0, c1, in_idx), may be
+ * NULL when max_units = 0; *n_units receives the full count.  *nk: slots per output row (mode
+ * > 0) or column chunks (mode 0); *partial_doubles: the partial-sum storage of all modes.
+ * INVALID_ARG for N outside 2..4, R outside 1..8, a size < 1, 2^32 or more elements,
+ * unit_elements < 1, or mode >= N. */
+int cpmg_batch_plan(int N, const int64_t* dims, int R, int64_t unit_elements, int mode, int64_t* units,
+                    int64_t max_units, int64_t* n_units, int* nk, int64_t* partial_doubles);
+
 /* ---- served form ---------------------------------------------------------------------- */
 /* A request server with continuous batching on the context.  Submitted CP-ALS problems (the
  * same problem statement as cpmg_batch_solve) queue in arrival order; a worker thread admits

@@ -81,6 +81,9 @@ _SIGS = {
                                C.POINTER(cpmg_result)]),
     "mg_fmg": (C.c_int, [_P, _P, C.POINTER(cpmg_tensor), _PP, _PP, C.c_int, C.POINTER(cpmg_opts),
                          C.POINTER(cpmg_result)]),
+    "cpmg_batch_plan": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_int64, C.c_int,
+                                  C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int64)]),
     "cpmg_hier_free": (None, [_P]),
     "cpmg_hier_levels": (C.c_int, [_P]),
     "cpmg_hier_level_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), _P, _PP]),
@@ -423,6 +426,22 @@ def mg_fmg(ctx, hier, Z, A_coarsest, A, nu=100, opts=None, **kw):
     s = lib().mg_fmg(ctx.h, hier.h, C.byref(d), _ptrs(A_coarsest), _ptrs(A), int(nu), C.byref(o), C.byref(r))
     _check(s, "mg_fmg")
     return result_dict(r)
+
+
+def batch_plan(dims, R, unit_elements, mode):
+    """The batched form's MTTKRP work units of one mode of one tensor (host only): an int64
+    array of rows (rb, k, c0, c1, in_idx), the slot count nk and the partial-sum doubles."""
+    N = len(dims)
+    d = (C.c_int64 * N)(*[int(v) for v in dims])
+    n = C.c_int64()
+    _check(lib().cpmg_batch_plan(N, d, int(R), int(unit_elements), int(mode), None, 0, C.byref(n), None, None),
+           "cpmg_batch_plan")
+    out = np.zeros((max(n.value, 1), 5), dtype=np.int64)
+    nk, tot = C.c_int(), C.c_int64()
+    _check(lib().cpmg_batch_plan(N, d, int(R), int(unit_elements), int(mode),
+                                 out.ctypes.data_as(C.POINTER(C.c_int64)), n.value, C.byref(n), C.byref(nk),
+                                 C.byref(tot)), "cpmg_batch_plan")
+    return out[:n.value], nk.value, tot.value
 
 
 def cpmg_decompose(ctx, Z, A, A_test, opts=None, **kw):

@@ -1496,6 +1496,43 @@ int cpmg_batch_solve(cpmg_ctx* c, int count, const cpmg_tensor* Z, const int* R,
   return worst;
 }
 
+int cpmg_batch_plan(int N, const int64_t* dims, int R, int64_t unit_elements, int mode, int64_t* units,
+                    int64_t max_units, int64_t* n_units, int* nk, int64_t* partial_doubles) {
+  if (N < 2 || N > kBModes || !dims || R < 1 || R > kBR || unit_elements < 1 || mode < 0 || mode >= N ||
+      !n_units || max_units < 0 || (max_units > 0 && !units))
+    return CPMG_INVALID_ARG;
+  BItem it;
+  std::memset(&it, 0, sizeof(it));
+  it.N = N;
+  it.R = R;
+  int64_t P = 1;
+  for (int m = 0; m < kBModes; ++m) {
+    it.dims[m] = m < N ? dims[m] : 1;
+    if (m < N && dims[m] < 1) return CPMG_INVALID_ARG;
+    P *= it.dims[m];
+  }
+  if (P >= (int64_t(1) << 32)) return CPMG_INVALID_ARG;
+  it.target = unit_elements;
+  std::vector<BItem> one(1, it);
+  std::vector<BUnit> u[kBModes];
+  int k[kBModes];
+  size_t po[kBModes], tot = 0;
+  plan_units(one, u, k, po, &tot);
+  *n_units = (int64_t)u[mode].size();
+  for (int64_t i = 0; i < std::min<int64_t>(max_units, (int64_t)u[mode].size()); ++i) {
+    const BUnit& x = u[mode][i];
+    int64_t* d = units + 5 * i;
+    d[0] = x.rb;
+    d[1] = x.k;
+    d[2] = x.c0;
+    d[3] = x.c1;
+    d[4] = x.in_idx;
+  }
+  if (nk) *nk = k[mode];
+  if (partial_doubles) *partial_doubles = (int64_t)tot;
+  return CPMG_OK;
+}
+
 int cpmg_server_config(cpmg_ctx* c, size_t hbm_budget_bytes, int max_active, int sweeps_per_launch,
                        int64_t unit_elements) {
   if (!c || max_active < 0 || sweeps_per_launch < 0 || unit_elements < 0) return CPMG_INVALID_ARG;
