@@ -168,10 +168,16 @@ int cpmg_ttm(cpmg_ctx* ctx, const cpmg_tensor* Z, const double* const* Rhat, con
  *  - Z, A, M: device pointers on the current device (Z->mem must be CPMG_MEM_DEVICE).
  *  - cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default stream).  The call
  *    only enqueues work: M is ready when the stream reaches that point.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - The first call on a device (and the first after the device's primary context was
+ *    destroyed and recreated, e.g. by cudaDeviceReset) looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call before any
+ *    stream capture.  Later calls in the same context reuse the address.
  *  - All calls share the array: calls whose work overlaps on the GPU (unordered streams)
  *    race and corrupt each other.  Calls ordered on one stream are safe.
+ *  - A status word at the start of the array is cleared by each call.  If a bounded
+ *    device-side wait of the MTTKRP kernel expires, the kernel raises that word and a last
+ *    kernel of the same call overwrites every entry of M with NaN: the call cannot report
+ *    the expiry in its return value (it only enqueues work), so a NaN in M is the signal.
  *  - Returns CPMG_OUT_OF_BUDGET when the problem's scratch (per-CTA partial sums and
  *    Khatri-Rao tables, even with the fewest work units) exceeds the array,
  *    CPMG_INVALID_ARG for bad shapes or pointers, CPMG_CUDA_ERROR on a failed CUDA call. */
