@@ -110,6 +110,12 @@ typedef struct {
                                         in split BF16 (3 products, FP32 accumulation); 0: FP32
                                         CUDA cores.  The coarse tensors only shape the FAS
                                         corrections, so either keeps the fine-level fixed point */
+  int dimension_tree;                /* 1: on third-order levels with I_3 > 6 R, form
+                                        W = Z x_3 A^(3)^T in one pass over Z and take the mode-1
+                                        and mode-2 MTTKRPs from W (two passes per sweep, two for
+                                        all three products at one point, instead of three); the
+                                        products are the same sums in another order.  0: one pass
+                                        per mode.  Not in the paper (a reuse of partial results). */
 } cpmg_opts;
 
 typedef struct {
@@ -246,9 +252,13 @@ int cpmg_decompose(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A,
 /* CP-ALS (Section 3: for n = 1..N, A^(n) <- Z_(n) Phi^(n) (Gamma^(n))^+, then Eq. ALSnorm;
  * components sorted by decreasing lambda at the end) on `count` independent tensors at once,
  * each stopping when its g of Eq. gradConv drops below opts->tol or after opts->max_als_iters
- * sweeps.  Z[t]: device tensor, order 2..4, float32 or float64, fewer than 2^32 elements;
- * R[t] in 1..8; A[t]: Z[t].N device float64 I_n x R column-major factor arrays (initial
- * guess in, result out), owned by the caller and not aliased between tensors.  opts: precision (FP32 / DF / MIXED / FP64, as
+ * sweeps.  Z[t]: tensor of order 2..4, float32 or float64, fewer than 2^32 elements;
+ * R[t] in 1..8; A[t]: Z[t].N float64 I_n x R column-major factor arrays (initial
+ * guess in, result out), owned by the caller and not aliased between tensors.  Memory: all
+ * device pointers (Z[t].mem == CPMG_MEM_DEVICE), or, when Z[0].mem == CPMG_MEM_HOST, all host
+ * pointers (every Z[t].mem must then be CPMG_MEM_HOST): the call copies every tensor and
+ * factor array into one device block, solves there and copies the factors back (pinned host
+ * buffers make the copies asynchronous DMA).  opts: precision (FP32 / DF / MIXED / FP64, as
  * for cp_als_sweep), tol, max_als_iters, mixed_switch; check_every > 0 = sweeps between
  * g evaluations (default 8 when <= 0; the last evaluation may come up to check_every - 1 sweeps
  * after g first fell below tol).  All sweeps of all tensors run in one cooperative persistent
@@ -308,7 +318,10 @@ int cpmg_server_stats(cpmg_ctx* ctx, double* p50_s, double* p99_s, double* req_p
  * kind: 0 = FP32 launches, 1 = float64-accurate (pairs of floats), 2 = FP64.  bytes_per_launch
  * is the algorithmic traffic: sizeof(z) * prod(I) + 4 R sum_n I_n.  kind 3 = the tensor-core
  * mode products of the restriction (finest level in the solvers, every one in cpmg_ttm), with
- * bytes_per_launch = 4 (numel in + numel out). */
+ * bytes_per_launch = 4 (numel in + numel out).  kind 4 = the launches of the batched kernel in
+ * cpmg_batch_solve, with bytes_per_launch the mean over launches of: for every tensor active at
+ * the launch, sizeof(z) * prod(I) per MTTKRP pass (N per sweep, N for the g evaluation) plus
+ * 16 R sum_n I_n per sweep (float64 factors read and written). */
 int cpmg_profile_enable(cpmg_ctx* ctx, int enable);
 int cpmg_profile_read(cpmg_ctx* ctx, int kind, double* total_ms, int64_t* launches,
                       double* bytes_per_launch);

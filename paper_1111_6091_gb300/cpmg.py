@@ -43,7 +43,7 @@ class cpmg_opts(C.Structure):
                 ("n_t", C.c_int), ("max_setup_cycles", C.c_int), ("stag_eps", C.c_double),
                 ("gs_sweeps", C.c_int), ("coarsest", C.c_int64 * MAX_MODES), ("als_fallback", C.c_int),
                 ("mixed_switch", C.c_double), ("check_every", C.c_int), ("use_graphs", C.c_int),
-                ("ttm_tensor_cores", C.c_int)]
+                ("ttm_tensor_cores", C.c_int), ("dimension_tree", C.c_int)]
 
 
 class cpmg_result(C.Structure):
@@ -268,7 +268,8 @@ def cpmg_ttm(ctx, Z, Rhat, tensor_cores=0):
 
 
 def cpmg_batch_solve(ctx, Zs, As, opts=None, **kw):
-    """Batched CP-ALS on the device tensors ``Zs`` with factor lists ``As`` (updated in place).
+    """Batched CP-ALS on the tensors ``Zs`` with factor lists ``As`` (updated in place): all on the
+    device, or all host (CPU, preferably pinned) tensors, which the library copies in and out.
     Returns (status, list of result dicts)."""
     o = opts or make_opts(**kw)
     n = len(Zs)

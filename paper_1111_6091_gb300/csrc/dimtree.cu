@@ -1,0 +1,267 @@
+// Contractions of the partial MTTKRP W = Z x_3 A^(3)^T for the first two modes (see dimtree.cuh).
+//
+// W is small next to Z (R I_1 I_2 float64 against I_1 I_2 I_3 values), so these kernels only need
+// to read it once with coalesced loads and enough loads in flight; the float64 arithmetic is one
+// FMA per loaded value.
+#include "dimtree.cuh"
+#include "mttkrp.cuh"
+
+namespace cpmg {
+
+constexpr int kDtPhases = 16;  // warps of the mode-0 kernel, each summing every 16th j
+
+// mode 0: block (32 lanes along i) x (16 warps along j), one r per blockIdx.y
+__global__ void __launch_bounds__(32 * kDtPhases) k_dt_mode0(const double* __restrict__ W, int64_t I1, int64_t I2,
+                                                           const double* __restrict__ V, double* out,
+                                                           int64_t ld_row, int64_t ld_col) {
+  __shared__ double red[kDtPhases][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+  const int r = blockIdx.y;
+  const double* Wr = W + (int64_t)r * I1 * I2;
+  const double* Vr = V + (int64_t)r * I2;
+  double acc = 0.0;
+  if (i < I1) {
+    int64_t j = w;
+    // four independent loads in flight per step, summed in a fixed order
+    for (; j + 3 * kDtPhases < I2; j += 4 * kDtPhases) {
+      const double a0 = Wr[i + I1 * j], a1 = Wr[i + I1 * (j + kDtPhases)];
+      const double a2 = Wr[i + I1 * (j + 2 * kDtPhases)], a3 = Wr[i + I1 * (j + 3 * kDtPhases)];
+      acc = fma(a0, Vr[j], acc);
+      acc = fma(a1, Vr[j + kDtPhases], acc);
+      acc = fma(a2, Vr[j + 2 * kDtPhases], acc);
+      acc = fma(a3, Vr[j + 3 * kDtPhases], acc);
+    }
+    for (; j < I2; j += kDtPhases) acc = fma(Wr[i + I1 * j], Vr[j], acc);
+  }
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && i < I1) {
+    double s = red[0][lane];
+    for (int q = 1; q < kDtPhases; ++q) s += red[q][lane];
+    out[i * ld_row + (int64_t)r * ld_col] = s;
+  }
+}
+
+// mode 1: one warp per (j, r), lanes along i, a fixed shuffle tree
+__global__ void __launch_bounds__(256) k_dt_mode1(const double* __restrict__ W, int64_t I1, int64_t I2, int R,
+                                                  const double* __restrict__ V, double* out, int64_t ld_row,
+                                                  int64_t ld_col) {
+  const int lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= I2 * R) return;
+  const int64_t j = item % I2;
+  const int r = (int)(item / I2);
+  const double* col = W + (int64_t)r * I1 * I2 + I1 * j;
+  const double* Vr = V + (int64_t)r * I1;
+  double acc = 0.0;
+  int64_t i = lane;
+  for (; i + 96 < I1; i += 128) {
+    const double a0 = col[i], a1 = col[i + 32], a2 = col[i + 64], a3 = col[i + 96];
+    acc = fma(a0, Vr[i], acc);
+    acc = fma(a1, Vr[i + 32], acc);
+    acc = fma(a2, Vr[i + 64], acc);
+    acc = fma(a3, Vr[i + 96], acc);
+  }
+  for (; i < I1; i += 32) acc = fma(col[i], Vr[i], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[j * ld_row + (int64_t)r * ld_col] = acc;
+}
+
+// ------------------------------------------------------------------ W = X C (one pass over X)
+constexpr int kWThreads = 128;
+constexpr int kWTile = 256;    // columns of C staged in shared memory at a time
+constexpr int kWUnroll = 8;    // columns of X whose loads are in flight together
+
+// accumulation per precision: FP32 fma; float pairs (the product's error and the TwoSum error of
+// the running sum go to the low word, folded back after every group of columns); float64 fma
+template <int PREC> struct WAcc;
+template <> struct WAcc<P_FP32> {
+  using A = float;
+  using S = float;
+  __device__ static S stage(double c) { return (float)c; }
+  __device__ static void add(A& a, float z, S c) { a = __fmaf_rn(z, c, a); }
+  __device__ static void add(A& a, double z, S c) { a = __fmaf_rn((float)z, c, a); }
+  __device__ static void norm(A&) {}
+  __device__ static double out(A a) { return (double)a; }
+};
+template <> struct WAcc<P_DF> {
+  using A = df;
+  using S = float2;
+  __device__ static S stage(double c) {
+    const df d = df_from_double(c);
+    return make_float2(d.hi, d.lo);
+  }
+  __device__ static void add(A& a, float z, S c) {
+    const float p = __fmul_rn(z, c.x);
+    float e = __fmaf_rn(z, c.x, -p);
+    e = __fmaf_rn(z, c.y, e);
+    const df s = df_two_sum(a.hi, p);
+    a.hi = s.hi;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, e));
+  }
+  __device__ static void norm(A& a) { a = df_two_sum(a.hi, a.lo); }
+  __device__ static double out(A a) { return df_to_double(a); }
+};
+template <> struct WAcc<P_FP64> {
+  using A = double;
+  using S = double;
+  __device__ static S stage(double c) { return c; }
+  __device__ static void add(A& a, float z, S c) { a = __fma_rn((double)z, c, a); }
+  __device__ static void add(A& a, double z, S c) { a = __fma_rn(z, c, a); }
+  __device__ static void norm(A&) {}
+  __device__ static double out(A a) { return a; }
+};
+
+template <typename TZ, int VW> struct WVec;
+template <typename TZ> struct WVec<TZ, 1> {
+  TZ v[1];
+  __device__ void load(const TZ* p) { v[0] = __ldg(p); }
+};
+template <> struct WVec<float, 2> {
+  float v[2];
+  __device__ void load(const float* p) {
+    const float2 x = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = x.x, v[1] = x.y;
+  }
+};
+template <> struct WVec<float, 4> {
+  float v[4];
+  __device__ void load(const float* p) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+  }
+};
+template <> struct WVec<double, 2> {
+  double v[2];
+  __device__ void load(const double* p) {
+    const double2 x = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = x.x, v[1] = x.y;
+  }
+};
+
+// Thread t of block b owns rows p0 .. p0 + VW - 1, p0 = (b * kWThreads + t) * VW (P % VW == 0 when
+// VW > 1), and walks every column k in increasing order: the sum over k has a fixed order.
+template <typename TZ, int PREC, int VW, int RP>
+__global__ void __launch_bounds__(kWThreads) k_dt_w(const TZ* __restrict__ X, int64_t P, int64_t K, int R,
+                                                    const double* __restrict__ C, double* __restrict__ W) {
+  using Acc = WAcc<PREC>;
+  using S = typename Acc::S;
+  __shared__ S cs[kWTile * RP];
+  const int64_t p0 = ((int64_t)blockIdx.x * kWThreads + threadIdx.x) * VW;
+  const bool live = p0 < P;
+  typename Acc::A acc[VW][RP];
+#pragma unroll
+  for (int v = 0; v < VW; ++v)
+#pragma unroll
+    for (int r = 0; r < RP; ++r) acc[v][r] = typename Acc::A{};
+  for (int64_t k0 = 0; k0 < K; k0 += kWTile) {
+    const int kt = (int)((K - k0) < kWTile ? (K - k0) : kWTile);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kt * RP; e += kWThreads) {
+      const int kk = e / RP, r = e % RP;
+      cs[e] = Acc::stage(r < R ? C[(k0 + kk) + K * r] : 0.0);
+    }
+    __syncthreads();
+    if (!live) continue;
+    const TZ* xp = X + p0 + P * k0;
+    int kk = 0;
+    for (; kk + kWUnroll <= kt; kk += kWUnroll) {
+      WVec<TZ, VW> x[kWUnroll];
+#pragma unroll
+      for (int u = 0; u < kWUnroll; ++u) x[u].load(xp + P * (kk + u));
+#pragma unroll
+      for (int u = 0; u < kWUnroll; ++u) {
+        const S* c = cs + (kk + u) * RP;
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const S cr = c[r];
+#pragma unroll
+          for (int v = 0; v < VW; ++v) Acc::add(acc[v][r], x[u].v[v], cr);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int r = 0; r < RP; ++r) Acc::norm(acc[v][r]);
+    }
+    for (; kk < kt; ++kk) {
+      WVec<TZ, VW> x;
+      x.load(xp + P * kk);
+      const S* c = cs + kk * RP;
+#pragma unroll
+      for (int r = 0; r < RP; ++r)
+#pragma unroll
+        for (int v = 0; v < VW; ++v) Acc::add(acc[v][r], x.v[v], c[r]);
+    }
+#pragma unroll
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int r = 0; r < RP; ++r) Acc::norm(acc[v][r]);
+  }
+  if (!live) return;
+#pragma unroll
+  for (int r = 0; r < RP; ++r)
+    if (r < R)
+#pragma unroll
+      for (int v = 0; v < VW; ++v) W[p0 + v + P * r] = Acc::out(acc[v][r]);
+}
+
+template <typename TZ, int PREC, int VW>
+static void launch_w_rp(const TZ* X, int64_t P, int64_t K, int R, const double* C, double* W, cudaStream_t st) {
+  const unsigned grid = (unsigned)((P / VW + kWThreads - 1) / kWThreads);
+  if (R <= 4) k_dt_w<TZ, PREC, VW, 4><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
+  else if (R <= 8) k_dt_w<TZ, PREC, VW, 8><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
+  else if (R <= 12) k_dt_w<TZ, PREC, VW, 12><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
+  else k_dt_w<TZ, PREC, VW, 16><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
+}
+
+int launch_dt_w(const void* X, int zdtype, int64_t P, int64_t K, int R, const double* C, int prec, double* W,
+                int num_sms, cudaStream_t st) {
+  if (R < 1 || R > 16 || P < 1 || K < 1) return CPMG_INVALID_ARG;
+  if (zdtype == CPMG_F64 && prec == P_DF) prec = P_FP64;
+  const uintptr_t xa = reinterpret_cast<uintptr_t>(X);
+  // rows per thread: wider vector loads while the grid still covers every SM about twice
+  auto fits = [&](int vw, int align) {
+    return P % vw == 0 && xa % align == 0 && (P / vw + kWThreads - 1) / kWThreads >= 2 * (int64_t)num_sms;
+  };
+  if (zdtype == CPMG_F64) {
+    const double* x = static_cast<const double*>(X);
+    const bool v2 = fits(2, 16);
+    if (prec == P_FP32) v2 ? launch_w_rp<double, P_FP32, 2>(x, P, K, R, C, W, st) : launch_w_rp<double, P_FP32, 1>(x, P, K, R, C, W, st);
+    else v2 ? launch_w_rp<double, P_FP64, 2>(x, P, K, R, C, W, st) : launch_w_rp<double, P_FP64, 1>(x, P, K, R, C, W, st);
+  } else {
+    const float* x = static_cast<const float*>(X);
+    const int vw = fits(4, 16) ? 4 : fits(2, 8) ? 2 : 1;
+    switch (prec) {
+      case P_FP32:
+        vw == 4 ? launch_w_rp<float, P_FP32, 4>(x, P, K, R, C, W, st)
+                : vw == 2 ? launch_w_rp<float, P_FP32, 2>(x, P, K, R, C, W, st)
+                          : launch_w_rp<float, P_FP32, 1>(x, P, K, R, C, W, st);
+        break;
+      case P_DF:
+        vw >= 2 ? launch_w_rp<float, P_DF, 2>(x, P, K, R, C, W, st) : launch_w_rp<float, P_DF, 1>(x, P, K, R, C, W, st);
+        break;
+      default:
+        vw >= 2 ? launch_w_rp<float, P_FP64, 2>(x, P, K, R, C, W, st) : launch_w_rp<float, P_FP64, 1>(x, P, K, R, C, W, st);
+    }
+  }
+  CPMG_CUDA_TRY(cudaGetLastError());
+  return CPMG_OK;
+}
+
+int launch_dt_contract(const double* W, int64_t I1, int64_t I2, int R, const double* V, int mode, double* out,
+                       int64_t ld_row, int64_t ld_col, cudaStream_t st) {
+  if (I1 < 1 || I2 < 1 || R < 1 || (mode != 0 && mode != 1)) return CPMG_INVALID_ARG;
+  if (mode == 0) {
+    const dim3 grid((unsigned)((I1 + 31) / 32), (unsigned)R);
+    k_dt_mode0<<<grid, 32 * kDtPhases, 0, st>>>(W, I1, I2, V, out, ld_row, ld_col);
+  } else {
+    const int64_t items = I2 * R;
+    k_dt_mode1<<<(unsigned)((items + 7) / 8), 256, 0, st>>>(W, I1, I2, R, V, out, ld_row, ld_col);
+  }
+  CPMG_CUDA_TRY(cudaGetLastError());
+  return CPMG_OK;
+}
+
+}  // namespace cpmg

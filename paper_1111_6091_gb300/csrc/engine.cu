@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "ctx.cuh"
 #include "dense.cuh"
+#include "dimtree.cuh"
 #include "fused.cuh"
 #include "mttkrp.cuh"
 #include "ttm.cuh"
@@ -53,9 +54,9 @@ struct cpmg_ctx {
   bool profile = false;
   std::vector<ProfEvents> pending;
   std::vector<ProfEvents> pool;
-  double prof_ms[4] = {0, 0, 0, 0};
-  int64_t prof_launches[4] = {0, 0, 0, 0};
-  double prof_bytes[4] = {0, 0, 0, 0};
+  double prof_ms[5] = {0, 0, 0, 0, 0};
+  int64_t prof_launches[5] = {0, 0, 0, 0, 0};
+  double prof_bytes[5] = {0, 0, 0, 0, 0};
   int64_t launches = 0;
   const void* prof_Z = nullptr;  // tensor whose MTTKRPs are profiled (the finest level)
   bool capturing = false;        // a CUDA graph capture is open on `stream`
@@ -267,6 +268,14 @@ static int prof_events(cpmg_ctx* c, int kind, double bytes, cudaEvent_t* e0, cud
   return CPMG_OK;
 }
 
+namespace cpmg {
+int ctx_profile_events(cpmg_ctx* c, int kind, double bytes, cudaEvent_t* e0, cudaEvent_t* e1) {
+  *e0 = *e1 = nullptr;
+  if (!c->profile) return CPMG_OK;
+  return prof_events(c, kind, bytes, e0, e1);
+}
+}  // namespace cpmg
+
 // Events for the tensor-core mode products of one restriction (2 per coarsened mode that runs
 // on tcgen05), with the algorithmic bytes of each (float in + float out).
 static int prof_ttm(cpmg_ctx* c, const Shape& s, int dtype, const double* const* Rh, const int64_t* Ic,
@@ -332,6 +341,7 @@ struct Level {
   double* H[kMaxModes] = {nullptr};
   double* buf = nullptr;   // backing store of F, H
   double* M = nullptr;     // I_max x R work
+  double* W = nullptr;     // I_1 x I_2 x R partial MTTKRP of the dimension tree (third order)
   double* twork = nullptr; // transform work (2 * Ic_max)
   double* blk = nullptr;   // block norms / weights (3 * (nt+1))
   bool coarsest() const {
@@ -340,6 +350,11 @@ struct Level {
     return true;
   }
 };
+
+// Third-order levels keep the dimension tree's W when it is small next to a pass over Z.
+static bool dt_worth(const Shape& s, int R) { return s.N == 3 && s.dims[2] > 6 * (int64_t)R; }
+
+constexpr int kBlkStride = 40;  // doubles of LS-weight bookkeeping per mode (Level::blk)
 
 struct cpmg_hier {
   cpmg_ctx* c = nullptr;
@@ -377,7 +392,8 @@ static int level_alloc(cpmg_ctx* c, Level& L, int R, int nt) {
   }
   CPMG_TRY(dalloc_t(c, &L.M, (size_t)imax * R));
   CPMG_TRY(dalloc_t(c, &L.twork, 2 * (size_t)icmax + 8));
-  CPMG_TRY(dalloc_t(c, &L.blk, 40));  // a2 @0, g2 @8, weights @16, |A Gamma|^2 @24
+  CPMG_TRY(dalloc_t(c, &L.blk, kBlkStride * kMaxModes));  // per mode: a2, g2, weights, |A Gamma|^2
+  if (dt_worth(L.s, R)) CPMG_TRY(dalloc_t(c, &L.W, (size_t)L.s.dims[0] * L.s.dims[1] * R));
   for (int n = 0; n < N; ++n)
     if (L.co[n]) {
       CPMG_TRY(dalloc_t(c, &L.Rhat[n], (size_t)L.cd[n] * L.s.dims[n]));
@@ -392,6 +408,7 @@ static void level_free(cpmg_ctx* c, Level& L) {
   for (auto& t : L.tf) fs_free(c, &t);
   dfree(c, L.buf);
   dfree(c, L.M);
+  dfree(c, L.W);
   dfree(c, L.twork);
   dfree(c, L.blk);
   dfree(c, L.Zown);
@@ -515,12 +532,95 @@ struct Solver {
   }
 };
 
+// ---------------------------------------------------------------- dimension tree (N = 3)
+// W = Z x_3 A^(3)^T is the mode-1 MTTKRP of the (I_1 I_2) x I_3 matricization, so the MTTKRP
+// kernels form it as they are; the mode-1 and mode-2 products then come from W (dimtree.cuh).
+// Worth it when W (R I_1 I_2 float64, written once, read twice) is small next to a pass over Z.
+static bool use_dt(const Solver& S, const Level& L, int R) {
+  return S.o.dimension_tree && L.W && dt_worth(L.s, R);
+}
+static int dt_form_w(Solver& S, const Level& L, const FactorSet& f, int prec) {
+  cpmg_ctx* c = S.c;
+  const int64_t P = L.s.dims[0] * L.s.dims[1], K = L.s.dims[2];
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profile && L.Z == c->prof_Z) {
+    // algorithmic traffic: Z once, A^(3) once, W written once
+    const double bytes = (L.dtype == CPMG_F64 ? 8.0 : 4.0) * (double)(P * K) + 8.0 * f.R * (double)(K + P);
+    const int eff = (L.dtype == CPMG_F64 && prec == P_DF) ? P_FP64 : prec;
+    CPMG_TRY(prof_events(c, eff == P_FP32 ? 0 : (eff == P_DF ? 1 : 2), bytes, &e0, &e1));
+  }
+  if (e0) CPMG_CUDA_TRY(cudaEventRecordWithFlags(e0, S.st, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+  CPMG_TRY(launch_dt_w(L.Z, L.dtype, P, K, f.R, f.A[2], prec, L.W, c->num_sms, S.st));
+  if (e1) CPMG_CUDA_TRY(cudaEventRecordWithFlags(e1, S.st, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+  c->launches += 1;
+  return CPMG_OK;
+}
+
+// The N products M^(n) = Z_(n) Phi^(n) at one point f (all modes, no update between them),
+// handed in mode order to use(n, M) with M = L.M (overwritten by the next mode).  With the
+// dimension tree this streams Z twice instead of N times.
+template <typename Fn>
+static int mttkrp_all(Solver& S, const Level& L, const FactorSet& f, int prec, Fn&& use) {
+  if (use_dt(S, L, f.R)) {
+    CPMG_TRY(dt_form_w(S, L, f, prec));
+    for (int n = 0; n < 2; ++n) {
+      CPMG_TRY(launch_dt_contract(L.W, L.s.dims[0], L.s.dims[1], f.R, n == 0 ? f.A[1] : f.A[0], n, L.M, 1,
+                                  L.s.dims[n], S.st));
+      S.c->launches += 1;
+      CPMG_TRY(use(n, L.M));
+    }
+    CPMG_TRY(run_mttkrp(S.c, L.s, L.Z, L.dtype, f, 2, prec, L.M));
+    return use(2, L.M);
+  }
+  for (int n = 0; n < f.N; ++n) {
+    CPMG_TRY(run_mttkrp(S.c, L.s, L.Z, L.dtype, f, n, prec, L.M));
+    CPMG_TRY(use(n, L.M));
+  }
+  return CPMG_OK;
+}
+
+// One relaxation sweep, modes in increasing order: kind 0 = ALS update (Section 3), kind 1 =
+// BNGS Gauss-Seidel update on A Gamma = M + F (Section 5.2).  `normalize_last`: Eq. ALSnorm in
+// the last mode's update.  With the dimension tree, modes 1 and 2 read W (A^(3) is unchanged
+// while they are updated) and only mode 3 streams Z again.
+static int sweep_modes(Solver& S, const Level& L, FactorSet& f, int prec, int kind, bool hasF,
+                       bool normalize_last) {
+  const int gs = kind == 1 ? S.o.gs_sweeps : 0;
+  if (use_dt(S, L, f.R)) {
+    CPMG_TRY(dt_form_w(S, L, f, prec));
+    // the products go to the fused update kernel as one float64 partial row per output row
+    MttkrpPlan q;
+    q.mode = 1;
+    q.nseg = 1;
+    q.C = 1;
+    q.nw = 1;
+    q.RP = f.R;
+    q.SEG = 1;
+    q.part_elem = 8;
+    MttkrpScratch w;
+    w.partial = S.c->mt_partial;
+    w.tables = S.c->mt_tables;
+    for (int n = 0; n < 2; ++n) {
+      CPMG_TRY(launch_dt_contract(L.W, L.s.dims[0], L.s.dims[1], f.R, n == 0 ? f.A[1] : f.A[0], n,
+                                  static_cast<double*>(S.c->mt_partial), f.R, 1, S.st));
+      CPMG_TRY(launch_finish_update(q, w, f, n, kind, hasF ? L.F[n] : nullptr, gs, nullptr, S.c->gscratch,
+                                    S.c->dstatus + 2, S.c->dstatus, S.st, false));
+      S.c->launches += 2;
+    }
+    return run_mttkrp_k(S.c, L.s, L.Z, L.dtype, f, 2, prec, nullptr, kind, hasF ? L.F[2] : nullptr, gs,
+                        normalize_last);
+  }
+  for (int n = 0; n < f.N; ++n)
+    CPMG_TRY(run_mttkrp_k(S.c, L.s, L.Z, L.dtype, f, n, prec, nullptr, kind, hasF ? L.F[n] : nullptr, gs,
+                          normalize_last && n == f.N - 1));
+  return CPMG_OK;
+}
+
 // One ALS iteration over all modes plus normalization (Section 3, Eq. ALSnorm).
 static int als_sweep(Solver& S, const Level& L, int lvl, FactorSet& f) {
   const int prec = S.prec_for(lvl, L.dtype);
   // the last mode's update also normalizes (Eq. ALSnorm) in its final block
-  for (int n = 0; n < f.N; ++n)
-    CPMG_TRY(run_mttkrp_k(S.c, L.s, L.Z, L.dtype, f, n, prec, nullptr, 0, nullptr, 0, n == f.N - 1));
+  CPMG_TRY(sweep_modes(S, L, f, prec, 0, false, true));
   if (lvl == 0 && prec != P_FP32) S.refine_sweeps++;
   return CPMG_OK;
 }
@@ -538,9 +638,7 @@ static int relax_als(Solver& S, const Level& L, int lvl, FactorSet& f, int iters
 static int relax_bngs(Solver& S, const Level& L, int lvl, FactorSet& f, bool hasF, int iters, bool top) {
   const int prec = S.prec_for(lvl, L.dtype);
   for (int it = 0; it < iters; ++it) {
-    for (int n = 0; n < f.N; ++n)
-      CPMG_TRY(run_mttkrp_k(S.c, L.s, L.Z, L.dtype, f, n, prec, nullptr, 1, hasF ? L.F[n] : nullptr,
-                            S.o.gs_sweeps));
+    CPMG_TRY(sweep_modes(S, L, f, prec, 1, hasF, false));
     if (lvl == 0 && prec != P_FP32) S.refine_sweeps++;
     if (top) {
       CPMG_TRY(launch_normalize(f, S.st));
@@ -556,12 +654,12 @@ static int relax_bngs(Solver& S, const Level& L, int lvl, FactorSet& f, bool has
 // host read after a synchronization.  Also yields ||M|| for the precision switch.
 static int eval_g_launch(Solver& S, const Level& L, FactorSet& f) {
   const int prec = S.gprec(L.dtype);
-  for (int n = 0; n < f.N; ++n) {
-    CPMG_TRY(run_mttkrp(S.c, L.s, L.Z, L.dtype, f, n, prec, L.M));
-    CPMG_TRY(launch_grad_sq(f, n, L.M, S.c->dsc, n, S.st));
-    CPMG_TRY(launch_sq_norm(L.M, L.s.dims[n] * f.R, S.c->dsc, 64 + n, S.st));
+  CPMG_TRY(mttkrp_all(S, L, f, prec, [&](int n, const double* M) -> int {
+    CPMG_TRY(launch_grad_sq(f, n, M, S.c->dsc, n, S.st));
+    CPMG_TRY(launch_sq_norm(M, L.s.dims[n] * f.R, S.c->dsc, 64 + n, S.st));
     S.c->launches += 2;
-  }
+    return CPMG_OK;
+  }));
   CPMG_CUDA_TRY(cudaMemcpyAsync(S.c->hsc, S.c->dsc, 128 * sizeof(double), cudaMemcpyDeviceToHost, S.st));
   CPMG_CUDA_TRY(cudaMemcpyAsync(S.c->hsc + 128, S.c->dstatus, 4 * sizeof(int), cudaMemcpyDeviceToHost, S.st));
   return CPMG_OK;
@@ -685,7 +783,7 @@ static int graph_run(Solver& S, const std::string& key, Fn&& body) {
 // planned or allocated while a graph is being captured.
 static int preplan(cpmg_ctx* c, const std::vector<const Level*>& levels, int R) {
   size_t part = 0, tab = 0;
-  for (const Level* L : levels)
+  for (const Level* L : levels) {
     for (int n = 0; n < L->s.N; ++n)
       for (int prec : {(int)P_FP32, (int)P_FP64, (int)P_DF}) {
         const MttkrpPlan* p = nullptr;
@@ -693,6 +791,9 @@ static int preplan(cpmg_ctx* c, const std::vector<const Level*>& levels, int R) 
         part = std::max(part, p->partial_bytes());
         tab = std::max(tab, p->tables_bytes());
       }
+    if (L->W)  // the dimension tree: float64 rows of the W products for the fused update
+      part = std::max(part, sizeof(double) * (size_t)std::max(L->s.dims[0], L->s.dims[1]) * R);
+  }
   return ensure_scratch(c, part, tab);
 }
 
@@ -737,24 +838,30 @@ static int build_operators(Solver& S, cpmg_hier* h, int lvl, bool first) {
   Level& L = h->L[lvl];
   const int R = h->R;
   const int prec = S.prec_for(lvl, L.dtype);
+  int nb = 0;
+  FactorSet* blocks[CPMG_MAX_TEST_BLOCKS + 1];
+  for (int t = 0; t < h->nt; ++t) blocks[nb++] = &L.tf[t];
+  if (!first) blocks[nb++] = &L.A;
+  // per block, the gradients of every coarsened mode at the block's point (one all-modes MTTKRP);
+  // mode n's norms sit at L.blk + kBlkStride n: a2 @0, g2 @8, weights @16, |A Gamma|^2 @24
+  for (int k = 0; k < nb; ++k)
+    CPMG_TRY(mttkrp_all(S, L, *blocks[k], prec, [&](int n, const double* M) -> int {
+      if (!L.co[n]) return CPMG_OK;
+      double* b = L.blk + kBlkStride * n;
+      CPMG_TRY(launch_sq_norm(blocks[k]->A[n], L.s.dims[n] * R, b, k, S.st));
+      CPMG_TRY(launch_grad_sq(*blocks[k], n, M, b, 8 + k, S.st, 24 + k));
+      S.c->launches += 2;
+      return CPMG_OK;
+    }));
   for (int n = 0; n < L.s.N; ++n) {
     if (!L.co[n]) continue;
     const double* U[CPMG_MAX_TEST_BLOCKS + 1];
-    int nb = 0;
-    FactorSet* blocks[CPMG_MAX_TEST_BLOCKS + 1];
-    for (int t = 0; t < h->nt; ++t) blocks[nb++] = &L.tf[t];
-    if (!first) blocks[nb++] = &L.A;
-    for (int k = 0; k < nb; ++k) {
-      U[k] = blocks[k]->A[n];
-      CPMG_TRY(launch_sq_norm(blocks[k]->A[n], L.s.dims[n] * R, L.blk, k, S.st));
-      CPMG_TRY(run_mttkrp(S.c, L.s, L.Z, L.dtype, *blocks[k], n, prec, L.M));
-      CPMG_TRY(launch_grad_sq(*blocks[k], n, L.M, L.blk, 8 + k, S.st, 24 + k));
-      S.c->launches += 2;
-    }
+    for (int k = 0; k < nb; ++k) U[k] = blocks[k]->A[n];
+    double* b = L.blk + kBlkStride * n;
     // a gradient at the rounding level of the MTTKRP that produced it counts as zero
     const double tau = prec == P_FP32 ? 1e-5 : 1e-12;
-    CPMG_TRY(launch_block_weights(nb, L.blk, L.blk + 8, L.blk + 24, tau, L.blk + 16, S.st));
-    CPMG_TRY(launch_interp(L.s.dims[n], R, nb, U, L.blk + 16, L.Pw[n], S.st));
+    CPMG_TRY(launch_block_weights(nb, b, b + 8, b + 24, tau, b + 16, S.st));
+    CPMG_TRY(launch_interp(L.s.dims[n], R, nb, U, b + 16, L.Pw[n], S.st));
     CPMG_TRY(launch_transform(L.s.dims[n], L.Pw[n], L.Rhat[n], L.twork, S.st));
     S.c->launches += 3;
   }
@@ -827,22 +934,25 @@ static int cp_fas(Solver& S, cpmg_hier* h, int lvl, bool hasF, int top) {
     CPMG_TRY(fs_copy(C.A, C.At, S.st));
     const int prec_f = S.prec_for(lvl, L.dtype);
     const int prec_c = S.prec_for(lvl + 1, C.dtype);
-    for (int n = 0; n < L.s.N; ++n) {
-      // r = F - H(A) on this level (Eq. FASrhs), kept in L.H[n]
-      CPMG_TRY(run_mttkrp(S.c, L.s, L.Z, L.dtype, L.A, n, prec_f, L.M));
-      CPMG_TRY(launch_fas_op(L.A, n, L.M, L.H[n], S.st));
+    // r = F - H(A) on this level (Eq. FASrhs), kept in L.H[n]: all modes at the point A
+    CPMG_TRY(mttkrp_all(S, L, L.A, prec_f, [&](int n, const double* M) -> int {
+      CPMG_TRY(launch_fas_op(L.A, n, M, L.H[n], S.st));
       if (hasF) CPMG_TRY(launch_axpby(L.s.dims[n] * R, 1.0, L.F[n], -1.0, L.H[n], S.st));
       else CPMG_TRY(launch_axpby(L.s.dims[n] * R, 0.0, L.H[n], -1.0, L.H[n], S.st));
-      // H_c(A~_c) into C.F[n]
-      CPMG_TRY(run_mttkrp(S.c, C.s, C.Z, C.dtype, C.At, n, prec_c, C.M));
-      CPMG_TRY(launch_fas_op(C.At, n, C.M, C.F[n], S.st));
+      return CPMG_OK;
+    }));
+    // H_c(A~_c) into C.F[n]: all modes at the point A~_c
+    CPMG_TRY(mttkrp_all(S, C, C.At, prec_c, [&](int n, const double* M) -> int {
+      return launch_fas_op(C.At, n, M, C.F[n], S.st);
+    }));
+    for (int n = 0; n < L.s.N; ++n) {
       // F_c = H_c(A~_c) + R-hat r   (identity for modes not coarsened)
       if (L.co[n])
         CPMG_TRY(launch_dgemm_small(false, L.cd[n], R, L.s.dims[n], 1.0, L.Rhat[n], L.cd[n], L.H[n],
                                     L.s.dims[n], 1.0, C.F[n], L.cd[n], S.st));
       else
         CPMG_TRY(launch_axpby(L.s.dims[n] * R, 1.0, L.H[n], 1.0, C.F[n], S.st));
-      S.c->launches += 5;
+      S.c->launches += 4;
     }
     CPMG_TRY(cp_fas(S, h, lvl + 1, true, top));
     for (int n = 0; n < L.s.N; ++n) {  // Eq. FASCGC: A += P-hat (A_c - A~_c)
@@ -985,6 +1095,7 @@ void cpmg_opts_default(cpmg_opts* o) {
   o->check_every = 1;
   o->use_graphs = 1;
   o->ttm_tensor_cores = 1;
+  o->dimension_tree = 1;
 }
 
 const char* cpmg_status_str(int s) {
@@ -1061,7 +1172,7 @@ int cpmg_profile_enable(cpmg_ctx* c, int enable) {
 }
 
 int cpmg_profile_read(cpmg_ctx* c, int kind, double* total_ms, int64_t* launches, double* bytes) {
-  if (!c || kind < 0 || kind > 3) return CPMG_INVALID_ARG;
+  if (!c || kind < 0 || kind > 4) return CPMG_INVALID_ARG;
   CPMG_TRY(profile_collect(c));
   if (total_ms) *total_ms = c->prof_ms[kind];
   if (launches) *launches = c->prof_launches[kind];
@@ -1072,7 +1183,7 @@ int cpmg_profile_read(cpmg_ctx* c, int kind, double* total_ms, int64_t* launches
 int cpmg_profile_reset(cpmg_ctx* c) {
   if (!c) return CPMG_INVALID_ARG;
   CPMG_TRY(profile_collect(c));
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     c->prof_ms[k] = 0;
     c->prof_launches[k] = 0;
     c->prof_bytes[k] = 0;
@@ -1201,6 +1312,8 @@ int cp_als_sweep(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A, int
   c->prof_Z = L.Z;
   if (st == CPMG_OK) st = fs_alloc(c, &fs, Z->N, R, L.s.dims);
   if (st == CPMG_OK) st = dalloc_t(c, &L.M, (size_t)imax * R);
+  if (st == CPMG_OK && opts->dimension_tree && dt_worth(L.s, R))
+    st = dalloc_t(c, &L.W, (size_t)L.s.dims[0] * L.s.dims[1] * R);
   if (st == CPMG_OK) st = dalloc_t(c, &S.sortbuf, fs_doubles(Z->N, R, L.s.dims));
   if (st == CPMG_OK) st = factors_in(c, Z->mem, A, fs);
   double z2 = 0, fv = 0, g = -1, gprev = -1, mn = 0;
@@ -1254,6 +1367,7 @@ int cp_als_sweep(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A, int
   if (st == CPMG_OK && (!std::isfinite(fv) || !std::isfinite(g))) st = CPMG_NUMERIC;
   if (st == CPMG_OK && opts->check_every != 0 && !conv && !(g < opts->tol)) st = CPMG_NOT_CONVERGED;
   if (res) res->status = st;
+  dfree(c, L.W);
   dfree(c, L.M);
   dfree(c, S.sortbuf);
   fs_free(c, &fs);

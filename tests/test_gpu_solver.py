@@ -249,3 +249,31 @@ def test_multilevel_fmg_on_the_papers_dense_tensor(cpmg_ctx):
     assert align.factor_error(ref.A, got) <= 1e-7
     _, it_als = ALS.als(Z, A0, 10000, tol=1e-10, g_fn=T.g_value)
     assert (r1["iters_setup"] + 1 + r2["iters_solve"]) * 20 < it_als
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_dimension_tree_sweeps_match_oracle(cpmg_ctx, dt):
+    """Third-order tensor with I_3 > 6R, so the sweeps take modes 1 and 2 from W = Z x_3 A^(3)^T:
+    three ALS sweeps with and without the dimension tree both match the oracle's ALS, and f and g
+    of the result (Eq. CPfunctional, Eq. gradConv) match the oracle's."""
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((36, 28, 44), 4, congruence=0.6, eta_homo=0.01, dtype=dt, seed=6)
+    Z64 = p.Z.astype(np.float64)
+    ref = p.A0
+    for _ in range(3):
+        ref = ALS.als_sweep(Z64, ref)
+    ref = ALS.sort_components(ref)
+    precs = ((cpmg.PREC_FP64, 1e-10),) + (((cpmg.PREC_DF, 1e-9), (cpmg.PREC_FP32, 2e-4)) if dt == np.float32 else ())
+    for prec, tol in precs:
+        for tree in (0, 1):
+            A = dev(cpmg, p.A0)
+            r = cpmg.cp_als_sweep(cpmg_ctx, cpmg.colmajor(p.Z), A, 3, precision=prec, check_every=0,
+                                  dimension_tree=tree)
+            got = host(cpmg, A)
+            for a, b in zip(got, ref):
+                assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(b)), (prec, tree)
+            f_got, f_ref = T.f_value(Z64, got), T.f_value(Z64, ref)
+            assert abs(r["f"] - f_got) <= 1e-9 * f_got
+            assert abs(r["g"] - T.g_value(Z64, got)) <= 1e-6 * T.g_value(Z64, got)
+            if prec != cpmg.PREC_FP32:
+                assert abs(f_got - f_ref) <= 1e-9 * f_ref
