@@ -1010,6 +1010,7 @@ static BTen make_desc(const BItem& it) {
 struct BatchDev {
   cpmg_ctx* c = nullptr;
   int nten = 0, maxN = 0, grid = 0;
+  int grid_run = 0;              // CTAs of the next launch: the loaded work's need, at most `grid`
   BTen* d_ten = nullptr;
   size_t cap_ten = 0;
   BUnit* d_units[kBModes] = {nullptr, nullptr, nullptr, nullptr};
@@ -1105,6 +1106,12 @@ static int batch_load(BatchDev& B, const std::vector<BItem>& items) {
     CPMG_CUDA_TRY(cudaMemcpyAsync(B.d_rows[n], rows[n].data(), rows[n].size() * sizeof(BRow),
                                   cudaMemcpyHostToDevice, st));
   }
+  // a smaller batch needs fewer CTAs: its phases have fewer units and rows than warps, and every
+  // grid barrier waits for each CTA of the launch
+  int64_t need = (int64_t)items.size();
+  for (int n = 0; n < kBModes; ++n)
+    need = std::max({need, cdiv64(B.nunits[n], kBWarps), cdiv64(B.nrows[n], kBWarps)});
+  B.grid_run = (int)std::max<int64_t>(1, std::min<int64_t>(need, B.grid));
   B.host.resize(items.size());
   bool any_init = false;
   for (size_t t = 0; t < items.size(); ++t) {
@@ -1126,7 +1133,21 @@ static int batch_load(BatchDev& B, const std::vector<BItem>& items) {
   return CPMG_OK;
 }
 
-static int launch_batch(BatchDev& B, int nsweeps, int eval) {
+// Algorithmic traffic of one launch: Z of every active tensor read once per MTTKRP pass (N per
+// sweep, N more for the g evaluation), plus its float64 factors read and written once per sweep.
+static double launch_bytes(const BatchDev& B, int nsweeps, int eval) {
+  double b = 0.0;
+  for (const BTen& T : B.host) {
+    if (!T.active) continue;
+    double P = 1.0, rows = 0.0;
+    for (int m = 0; m < T.N; ++m) P *= (double)T.dims[m], rows += (double)T.dims[m];
+    const double zb = (T.zf64 ? 8.0 : 4.0) * P;
+    b += (double)(nsweeps * T.N + (eval ? T.N : 0)) * zb + (double)nsweeps * 16.0 * T.R * rows;
+  }
+  return b;
+}
+
+static int launch_batch(BatchDev& B, int nsweeps, int eval, bool profile = false) {
   cudaStream_t st = ctx_stream(B.c);
   BArgs a;
   a.ten = B.d_ten;
@@ -1146,15 +1167,20 @@ static int launch_batch(BatchDev& B, int nsweeps, int eval) {
   void* args[] = {&a};
   CPMG_CUDA_TRY(cudaMemsetAsync(B.d_flags + 1, 0, sizeof(int), st));
   CPMG_CUDA_TRY(cudaMemsetAsync(B.d_bar, 0, 2 * sizeof(unsigned), st));
-  CPMG_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_batch, dim3(B.grid), dim3(kBThreads), args, 0, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (profile) CPMG_TRY(ctx_profile_events(B.c, 4, launch_bytes(B, nsweeps, eval), &e0, &e1));
+  if (e0) CPMG_CUDA_TRY(cudaEventRecord(e0, st));
+  const int grid = B.grid_run > 0 ? B.grid_run : B.grid;
+  CPMG_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_batch, dim3(grid), dim3(kBThreads), args, 0, st));
+  if (e1) CPMG_CUDA_TRY(cudaEventRecord(e1, st));
   ctx_add_launches(B.c, 1);
   return CPMG_OK;
 }
 
 // k sweeps + one evaluation; refreshes the host mirror of every descriptor.
-static int batch_step(BatchDev& B, int k, int* nactive) {
+static int batch_step(BatchDev& B, int k, int* nactive, bool profile = false) {
   cudaStream_t st = ctx_stream(B.c);
-  CPMG_TRY(launch_batch(B, k, 1));
+  CPMG_TRY(launch_batch(B, k, 1, profile));
   CPMG_CUDA_TRY(cudaMemcpyAsync(B.h_flags, B.d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CPMG_CUDA_TRY(cudaMemcpyAsync(B.host.data(), B.d_ten, B.host.size() * sizeof(BTen), cudaMemcpyDeviceToHost, st));
   CPMG_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1443,10 +1469,80 @@ using namespace cpmg;
 
 extern "C" {
 
+static int batch_solve_dev(cpmg_ctx* c, int count, const cpmg_tensor* Z, const int* R, double* const* const* A,
+                           const cpmg_opts* opts, cpmg_result* results);
+
+// Host buffers: every tensor and its factors are copied into one device arena, solved there, and
+// the factors copied back; the copies are part of the call.
+static int batch_solve_host(cpmg_ctx* c, int count, const cpmg_tensor* Z, const int* R, double* const* const* A,
+                            const cpmg_opts* opts, cpmg_result* results) {
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  size_t total = 0;
+  for (int t = 0; t < count; ++t) {
+    if (Z[t].mem != CPMG_MEM_HOST || !Z[t].data || !A[t] || Z[t].N < 2 || Z[t].N > kBModes || R[t] < 1 ||
+        R[t] > kBR || (Z[t].dtype != CPMG_F32 && Z[t].dtype != CPMG_F64))
+      return CPMG_INVALID_ARG;
+    int64_t P = 1;
+    for (int m = 0; m < Z[t].N; ++m) {
+      if (Z[t].dims[m] < 1 || !A[t][m]) return CPMG_INVALID_ARG;
+      P *= Z[t].dims[m];
+      total += up(sizeof(double) * Z[t].dims[m] * R[t]);
+    }
+    total += up((Z[t].dtype == CPMG_F64 ? 8 : 4) * (size_t)P);
+  }
+  unsigned char* arena = nullptr;
+  CPMG_TRY(ctx_alloc(c, reinterpret_cast<void**>(&arena), total));
+  cudaStream_t st = ctx_stream(c);
+  std::vector<cpmg_tensor> dz(Z, Z + count);
+  std::vector<double*> dptr((size_t)count * kBModes, nullptr);
+  std::vector<double* const*> da(count);
+  size_t off = 0;
+  int rc = CPMG_OK;
+  for (int t = 0; t < count && rc == CPMG_OK; ++t) {
+    int64_t P = 1;
+    for (int m = 0; m < Z[t].N; ++m) P *= Z[t].dims[m];
+    const size_t zb = (Z[t].dtype == CPMG_F64 ? 8 : 4) * (size_t)P;
+    dz[t].data = arena + off;
+    dz[t].mem = CPMG_MEM_DEVICE;
+    if (cudaMemcpyAsync(arena + off, Z[t].data, zb, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = CPMG_CUDA_ERROR;
+    off += up(zb);
+    for (int m = 0; m < Z[t].N && rc == CPMG_OK; ++m) {
+      const size_t ab = sizeof(double) * Z[t].dims[m] * R[t];
+      dptr[(size_t)t * kBModes + m] = reinterpret_cast<double*>(arena + off);
+      if (cudaMemcpyAsync(arena + off, A[t][m], ab, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = CPMG_CUDA_ERROR;
+      off += up(ab);
+    }
+    da[t] = dptr.data() + (size_t)t * kBModes;
+  }
+  if (rc == CPMG_OK) rc = batch_solve_dev(c, count, dz.data(), R, da.data(), opts, results);
+  const bool copy_back = rc == CPMG_OK || rc == CPMG_NOT_CONVERGED;
+  for (int t = 0; t < count && copy_back; ++t)
+    for (int m = 0; m < Z[t].N; ++m)
+      if (cudaMemcpyAsync(A[t][m], dptr[(size_t)t * kBModes + m], sizeof(double) * Z[t].dims[m] * R[t],
+                          cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = CPMG_CUDA_ERROR;
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == CPMG_OK) rc = CPMG_CUDA_ERROR;
+  ctx_free(c, arena);
+  return rc;
+}
+
 int cpmg_batch_solve(cpmg_ctx* c, int count, const cpmg_tensor* Z, const int* R, double* const* const* A,
                      const cpmg_opts* opts, cpmg_result* results) {
   cudaGetLastError();
   if (!c || count < 1 || !Z || !R || !A || !opts || !results) return CPMG_INVALID_ARG;
+  if (Z[0].mem == CPMG_MEM_HOST) {
+    {
+      BatchState* S = state_of(c);
+      std::lock_guard<std::mutex> lk(S->mu);
+      if (S->started) return CPMG_INVALID_ARG;  // the context serves requests
+    }
+    return batch_solve_host(c, count, Z, R, A, opts, results);
+  }
+  return batch_solve_dev(c, count, Z, R, A, opts, results);
+}
+
+static int batch_solve_dev(cpmg_ctx* c, int count, const cpmg_tensor* Z, const int* R, double* const* const* A,
+                           const cpmg_opts* opts, cpmg_result* results) {
   {
     BatchState* S = state_of(c);
     std::lock_guard<std::mutex> lk(S->mu);
@@ -1471,15 +1567,45 @@ int cpmg_batch_solve(cpmg_ctx* c, int count, const cpmg_tensor* Z, const int* R,
   }
   if (st == CPMG_OK) st = batch_load(B, items);
   const int k = opts->check_every > 0 ? opts->check_every : 8;
+  // loaded[j]: the tensor in slot j of the loaded batch; last[t]: tensor t's latest device state
+  std::vector<int> loaded(count);
+  for (int t = 0; t < count; ++t) loaded[t] = t;
+  std::vector<BTen> last(count);
   if (st == CPMG_OK) {
     const int64_t maxl = (std::max(opts->max_als_iters, 1) + k - 1) / k + 2;
     int nact = count;
-    for (int64_t l = 0; l < maxl && nact > 0 && st == CPMG_OK; ++l) st = batch_step(B, k, &nact);
+    for (int64_t l = 0; l < maxl && nact > 0 && st == CPMG_OK; ++l) {
+      st = batch_step(B, k, &nact, true);
+      if (st != CPMG_OK || nact == 0 || nact * 2 > (int)loaded.size()) continue;
+      // at most half the loaded tensors still run: reload only those (their state carries over;
+      // each tensor's units, partial slots and sums are its own, so its arithmetic is unchanged)
+      std::vector<BItem> act;
+      std::vector<int> idx;
+      for (size_t j = 0; j < loaded.size(); ++j) {
+        last[loaded[j]] = B.host[j];
+        if (!B.host[j].active) continue;
+        BItem it = items[loaded[j]];
+        it.has_state = true;
+        it.state = B.host[j];
+        act.push_back(it);
+        idx.push_back(loaded[j]);
+      }
+      st = batch_load(B, act);
+      loaded.swap(idx);
+    }
+    for (size_t j = 0; j < loaded.size() && st == CPMG_OK; ++j) last[loaded[j]] = B.host[j];
   }
   if (st == CPMG_OK) {
+    if ((int)loaded.size() != count) {  // every tensor back in, with its final state, for the sort
+      for (int t = 0; t < count; ++t) {
+        items[t].has_state = true;
+        items[t].state = last[t];
+      }
+      st = batch_load(B, items);
+    }
     std::vector<int> all(count);
     for (int t = 0; t < count; ++t) all[t] = t;
-    st = batch_sort(B, all);
+    if (st == CPMG_OK) st = batch_sort(B, all);
   }
   const double dt = now_sec() - t0;
   int worst = st;
