@@ -71,6 +71,9 @@ struct BTen {
   int status;
   int iters, max_iters;
   int stall;
+  int check_k;                  // sweeps between this tensor's g evaluations (0: the launch's sweeps)
+  int next_check;               // iteration count at which its next evaluation is due
+  double g_prev;                // g at its previous evaluation
   double znorm2;
   double tol, mixed_switch;
   double g, g_best, f;
@@ -101,6 +104,8 @@ struct BArgs {
   int nsweeps;
   int eval;                     // 1: evaluate g and decide; 2: MTTKRP phases only (autotuner)
   unsigned* bar;                // [0] arrivals, [1] generation
+  unsigned bar_extra;           // 0; 1 only under the failure-detection test hook
+  unsigned long long wait_ns;   // limit of each bounded barrier wait
   int* err;
   int* nactive;
 };
@@ -209,7 +214,10 @@ __device__ __forceinline__ uint64_t bclock() {
   return t;
 }
 
-__device__ bool grid_sync(unsigned* bar, int* err) {
+// Every CTA arrives once; the last of gridDim.x + extra arrivals releases the others.  extra is 0
+// except under the failure-detection test hook, where 1 makes the barrier unreachable and every
+// wait run out after wait_ns (the kernel then reports error bit 2 and returns).
+__device__ bool grid_sync(unsigned* bar, int* err, unsigned extra, unsigned long long wait_ns) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -217,14 +225,14 @@ __device__ bool grid_sync(unsigned* bar, int* err) {
     const unsigned g = *gen;
     __threadfence();
     int ok = 1;
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    if (atomicAdd(bar, 1u) == gridDim.x + extra - 1) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
       const uint64_t t0 = bclock();
       while (*gen == g) {
-        if (bclock() - t0 > 2000000000ull) {
+        if (bclock() - t0 > wait_ns) {
           atomicOr(err, 2);
           ok = 0;
           break;
@@ -413,13 +421,19 @@ __device__ __forceinline__ void unit_dispatch(const BTen& T, const BUnit& u, int
   else unit_run<P, TZ, 8>(T, u, lane, ws, wc);
 }
 
+// The g evaluation of a launch covers the active tensors whose own check is due (or that reached
+// their sweep cap); the others only sweep.
+__device__ __forceinline__ bool eval_due(const BTen& T) {
+  return T.active && (T.iters >= T.next_check || (T.max_iters > 0 && T.iters >= T.max_iters));
+}
+
 __device__ void phase_units(const BArgs& a, int n, bool eval, BSmem& sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * kBWarps + warp, nw = (int64_t)gridDim.x * kBWarps;
   for (int64_t ui = gw; ui < a.nunits[n]; ui += nw) {
     const BUnit u = a.units[n][ui];
     const BTen& T = a.ten[u.t];
-    if (!T.active) continue;
+    if (!T.active || (eval && !eval_due(T))) continue;
     const int p = eval ? T.gprec : T.prec;
     if (T.zf64) unit_dispatch<BP_FP64, double>(T, u, lane, sm.ws[warp], sm.wc[warp]);
     else if (p == BP_FP32) unit_dispatch<BP_FP32, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
@@ -428,14 +442,19 @@ __device__ void phase_units(const BArgs& a, int n, bool eval, BSmem& sm) {
   }
 }
 
-// deterministic block sum of one value per thread (thread 0 adds in thread order)
+// deterministic block sum of one value per thread: a fixed butterfly inside each warp, then the
+// warp sums in warp order (13 dependent float64 adds at 256 threads instead of 256; GB300's float64
+// add latency is tens of cycles)
 __device__ double bblock_sum(double v, double* buf) {
-  buf[threadIdx.x] = v;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) buf[warp] = v;
   __syncthreads();
   __shared__ double tot;
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < (int)blockDim.x; ++k) s += buf[k];
+    double s = buf[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) s += buf[k];
     tot = s;
   }
   __syncthreads();
@@ -669,7 +688,7 @@ __device__ void phase_rows(const BArgs& a, const BRow* items, int64_t nitems, bo
   for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BRow rw = items[it];
     const BTen& T = a.ten[rw.t];
-    if (!T.active) continue;
+    if (!T.active || (!update && !eval_due(T))) continue;
     const int n = rw.mode;
     const int64_t i = rw.r0 + warp;
     if (i >= T.dims[n]) continue;
@@ -680,7 +699,7 @@ __device__ void phase_rows(const BArgs& a, const BRow* items, int64_t nitems, bo
   }
 }
 
-__device__ void check_tensor(BTen& T, int* nactive, BSmem& sm) {
+__device__ void check_tensor(BTen& T, int* nactive, int launch_k, BSmem& sm) {
   // sum over (r, c) of prod_n Upsilon^(n)_{rc} = ||[[A]]||^2, spread over threads
   double part = 0.0;
   for (int e = threadIdx.x; e < T.R * T.R; e += blockDim.x) {
@@ -742,7 +761,20 @@ __device__ void check_tensor(BTen& T, int* nactive, BSmem& sm) {
     }
     if (g < floor_g || T.stall >= 20) T.prec = BP_DF;
   }
-  if (T.active) atomicAdd(nactive, 1);
+  if (T.active) {
+    // next interval: about half the sweeps the observed rate predicts are left, a power-of-two
+    // multiple of the launch's sweeps, at most 32 (and the launch's sweeps while g is not falling)
+    int k = launch_k;
+    if (T.g_prev > 0.0 && g < T.g_prev && T.tol > 0.0 && g > T.tol) {
+      const int kp = T.check_k > 0 ? T.check_k : launch_k;
+      const double left = kp * log(T.tol / g) / log(g / T.g_prev);
+      while (2 * k <= 32 && 2 * k <= 0.5 * left) k *= 2;
+    }
+    T.check_k = k;
+    T.next_check = T.iters + k;
+    T.g_prev = g;
+    atomicAdd(nactive, 1);
+  }
 }
 
 __global__ void __launch_bounds__(kBThreads, 2) k_batch(BArgs a) {
@@ -750,10 +782,10 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batch(BArgs a) {
   bool ok = true;
   for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
     for (int n = 0; n < a.maxN && ok; ++n) {
-      phase_units(a, n, false, sm);
-      ok = grid_sync(a.bar, a.err);
+      if (n == 0) phase_units(a, 0, false, sm);  // later modes' units ran after the previous tensor phase
+      ok = grid_sync(a.bar, a.err, a.bar_extra, a.wait_ns);
       if (ok) phase_rows(a, a.rows[n], a.nrows[n], true);
-      ok = ok && grid_sync(a.bar, a.err);
+      ok = ok && grid_sync(a.bar, a.err, a.bar_extra, a.wait_ns);
       // per tensor: the Gram of the new A^(n); after the last mode Eq. ALSnorm; then Gamma^+
       // of the next mode to update
       for (int t = blockIdx.x; t < a.nten && ok; t += gridDim.x) {
@@ -764,21 +796,32 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batch(BArgs a) {
         if (last_mode) normalize_tensor(T, sm);
         gamma_inverse(T, last_mode ? 0 : n + 1, sm);
       }
-      ok = ok && grid_sync(a.bar, a.err);
+      // Mode n+1's MTTKRP units need the factors as the rows phase left them; a tensor's tensor
+      // phase changes its factors only after its last mode (Eq. ALSnorm), and such a tensor has
+      // no units of mode n+1.  So each CTA goes on to its share of those units without a grid
+      // barrier; Gamma^+ of mode n+1 is read only by the rows phase, after the next barrier.  The
+      // sweep boundary keeps its barrier: every normalization precedes the next sweep's units.
+      if (ok && n + 1 < a.maxN) phase_units(a, n + 1, false, sm);
+      else ok = ok && grid_sync(a.bar, a.err, a.bar_extra, a.wait_ns);
     }
   }
   if (a.eval && ok) {
     for (int n = 0; n < a.maxN; ++n) phase_units(a, n, a.eval == 1, sm);
     if (a.eval == 1)
       for (int t = blockIdx.x; t < a.nten; t += gridDim.x)
-        if (a.ten[t].active) gamma_all(a.ten[t]);
-    ok = grid_sync(a.bar, a.err);
+        if (eval_due(a.ten[t])) gamma_all(a.ten[t]);
+    ok = grid_sync(a.bar, a.err, a.bar_extra, a.wait_ns);
     if (a.eval == 1 && ok) {
       for (int n = 0; n < a.maxN; ++n) phase_rows(a, a.rows[n], a.nrows[n], false);
-      ok = grid_sync(a.bar, a.err);
+      ok = grid_sync(a.bar, a.err, a.bar_extra, a.wait_ns);
       for (int t = blockIdx.x; t < a.nten && ok; t += gridDim.x) {
-        if (!a.ten[t].active) continue;
-        check_tensor(a.ten[t], a.nactive, sm);
+        BTen& T = a.ten[t];
+        if (!T.active) continue;
+        if (!eval_due(T)) {  // still running, evaluated at a later launch
+          if (threadIdx.x == 0) atomicAdd(a.nactive, 1);
+          continue;
+        }
+        check_tensor(T, a.nactive, a.nsweeps, sm);
         __syncthreads();
       }
     }
@@ -1011,6 +1054,8 @@ struct BatchDev {
   cpmg_ctx* c = nullptr;
   int nten = 0, maxN = 0, grid = 0;
   int grid_run = 0;              // CTAs of the next launch: the loaded work's need, at most `grid`
+  unsigned bar_extra = 0;        // grid-barrier settings (see BArgs)
+  unsigned long long wait_ns = 2000000000ull;
   BTen* d_ten = nullptr;
   size_t cap_ten = 0;
   BUnit* d_units[kBModes] = {nullptr, nullptr, nullptr, nullptr};
@@ -1162,6 +1207,8 @@ static int launch_batch(BatchDev& B, int nsweeps, int eval, bool profile = false
   a.nsweeps = nsweeps;
   a.eval = eval;
   a.bar = B.d_bar;
+  a.bar_extra = B.bar_extra;
+  a.wait_ns = B.wait_ns;
   a.err = B.d_flags;
   a.nactive = B.d_flags + 1;
   void* args[] = {&a};
@@ -1213,6 +1260,7 @@ struct BatchState {
     std::chrono::steady_clock::time_point t_submit, t_done;
     cpmg_result res;
     int state;     // 0 queued, 1 running, 2 done
+    bool cancel = false;  // cpmg_server_cancel on a running request: retire at the next boundary
     size_t bytes;  // HBM held while running (tensor, factors, partials, Gram)
   };
   std::mutex mu;
@@ -1228,6 +1276,9 @@ struct BatchState {
   size_t budget = 0, reserved = 0;
   int max_active = 1024;
   int sweeps_per_launch = 8;
+  // failure-detection test hook (cpmg_debug_config): barrier wait limit, unreachable barrier
+  double wait_limit_s = 2.0;
+  int unreachable_barrier = 0;
   std::chrono::steady_clock::time_point t_first, t_last;
   bool any = false;
   int64_t completed = 0;
@@ -1395,9 +1446,12 @@ static void server_loop(cpmg_ctx* c, BatchState* S) {
     if ((rc = batch_step(B, S->sweeps_per_launch, &nact)) != CPMG_OK) break;
     S->launches += 1;
     std::vector<int> fin;
-    for (size_t t = 0; t < S->active.size(); ++t) {
-      S->active[t]->item.state = B.host[t];
-      if (!B.host[t].active) fin.push_back((int)t);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);  // cancel flags are set by other threads
+      for (size_t t = 0; t < S->active.size(); ++t) {
+        S->active[t]->item.state = B.host[t];
+        if (!B.host[t].active || S->active[t]->cancel) fin.push_back((int)t);
+      }
     }
     if (!fin.empty()) {
       if ((rc = batch_sort(B, fin)) != CPMG_OK) break;
@@ -1412,6 +1466,7 @@ static void server_loop(cpmg_ctx* c, BatchState* S) {
           q->t_done = now;
           const double lat = std::chrono::duration<double>(now - q->t_submit).count();
           fill_result(B.host[t], &q->res, lat);
+          if (q->cancel && B.host[t].active) q->res.status = CPMG_CANCELLED;  // stopped before its end
           q->state = 2;
           S->reserved -= q->bytes;
           S->lat.push_back(lat);
@@ -1554,6 +1609,11 @@ static int batch_solve_dev(cpmg_ctx* c, int count, const cpmg_tensor* Z, const i
   BatchDev B;
   double* grams = nullptr;
   int st = batch_open(c, B);
+  {
+    BatchState* S = state_of(c);
+    B.bar_extra = S->unreachable_barrier ? 1u : 0u;
+    B.wait_ns = (unsigned long long)(S->wait_limit_s * 1e9);
+  }
   size_t aux_total = 0;
   for (int t = 0; t < count; ++t) aux_total += aux_doubles(items[t]);
   if (st == CPMG_OK) st = ctx_alloc(c, reinterpret_cast<void**>(&grams), aux_total * sizeof(double));
@@ -1656,6 +1716,39 @@ int cpmg_batch_plan(int N, const int64_t* dims, int R, int64_t unit_elements, in
   }
   if (nk) *nk = k[mode];
   if (partial_doubles) *partial_doubles = (int64_t)tot;
+  return CPMG_OK;
+}
+
+int cpmg_server_cancel(cpmg_ctx* c, uint64_t ticket) {
+  if (!c) return CPMG_INVALID_ARG;
+  BatchState* S = state_of(c);
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto f = S->reqs.find(ticket);
+  if (f == S->reqs.end()) return CPMG_INVALID_ARG;
+  BatchState::Req* q = f->second;
+  if (q->state == 0) {  // still queued: leaves the queue now, its factors untouched
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it)
+      if (*it == q) {
+        S->queue.erase(it);
+        break;
+      }
+    std::memset(&q->res, 0, sizeof(q->res));
+    q->res.status = CPMG_CANCELLED;
+    q->res.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - q->t_submit).count();
+    q->state = 2;
+    S->cv.notify_all();
+  } else if (q->state == 1) {
+    q->cancel = true;  // the worker retires it after the launch in flight
+  }
+  return CPMG_OK;
+}
+
+int cpmg_debug_config(cpmg_ctx* c, double wait_limit_s, int unreachable_barrier) {
+  if (!c || !(wait_limit_s > 0.0) || wait_limit_s > 60.0) return CPMG_INVALID_ARG;
+  BatchState* S = state_of(c);
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->wait_limit_s = wait_limit_s;
+  S->unreachable_barrier = unreachable_barrier != 0;
   return CPMG_OK;
 }
 

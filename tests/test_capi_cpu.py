@@ -41,6 +41,7 @@ def test_opts_default_is_the_paper_table(lib):
     # additions that are not in the paper's table: MIXED policy with switch factor 4, no ALS
     # fallback unless asked for
     assert o.precision == cpmg.PREC_MIXED and o.mixed_switch == 4.0 and o.als_fallback == 0
+    assert o.dimension_tree == 1 and o.ttm_tensor_cores == 1
 
 
 def test_status_strings(lib):
@@ -67,6 +68,8 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.cpmg_server_wait(None, 0.0) == cpmg.INVALID_ARG
     assert lib.cpmg_server_config(None, 0, 0, 0, 0) == cpmg.INVALID_ARG
     assert lib.cpmg_server_stats(None, None, None, None, None) == cpmg.INVALID_ARG
+    assert lib.cpmg_server_cancel(None, 1) == cpmg.INVALID_ARG
+    assert lib.cpmg_debug_config(None, 1.0, 0) == cpmg.INVALID_ARG
 
 
 def test_struct_layout_matches_header(lib):
