@@ -68,7 +68,12 @@ typedef enum {
   CPMG_PREC_FP32 = 0,   /* float products, float accumulation (fastest; g floor ~1e-7 relative) */
   CPMG_PREC_FP64 = 1,   /* float64 products and accumulation: the plain FP64 path               */
   CPMG_PREC_MIXED = 2,  /* FP32 sweeps, then float64-accurate sweeps once g nears the FP32 floor */
-  CPMG_PREC_DF = 3      /* float64-accurate sweeps from the start (pairs of floats)              */
+  CPMG_PREC_DF = 3,     /* float64-accurate sweeps from the start (pairs of floats)              */
+  CPMG_PREC_BF16X3 = 4, /* split-BF16 MTTKRPs on tcgen05 tensor cores: x = hi + lo in BF16, the
+                           products hi*hi + hi*lo + lo*hi accumulated in FP32 (relative error near
+                           2^-16 per product); third-order float tensors with I_3 > 6R (the
+                           dimension tree's two passes), FP32 sweeps elsewhere                   */
+  CPMG_PREC_MIXED_BF16 = 5 /* as MIXED, with split-BF16 sweeps before the switch                  */
 } cpmg_precision;
 
 typedef struct cpmg_ctx cpmg_ctx;    /* device, stream, workspaces, statistics            */
@@ -259,9 +264,11 @@ int cpmg_decompose(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A,
  * pointers (every Z[t].mem must then be CPMG_MEM_HOST): the call copies every tensor and
  * factor array into one device block, solves there and copies the factors back (pinned host
  * buffers make the copies asynchronous DMA).  opts: precision (FP32 / DF / MIXED / FP64, as
- * for cp_als_sweep), tol, max_als_iters, mixed_switch; check_every > 0 = sweeps between
- * g evaluations (default 8 when <= 0; the last evaluation may come up to check_every - 1 sweeps
- * after g first fell below tol).  All sweeps of all tensors run in one cooperative persistent
+ * for cp_als_sweep), tol, max_als_iters, mixed_switch; check_every > 0 = sweeps per launch and
+ * between a tensor's first g evaluations (default 8 when <= 0).  Each tensor then sets its own
+ * interval from its observed rate: about half the sweeps the rate predicts are left, a power-of-two
+ * multiple of check_every up to 32, back to check_every while g does not fall; so its last
+ * evaluation may come up to interval - 1 sweeps after g first fell below tol.  All sweeps of all tensors run in one cooperative persistent
  * kernel per check interval; each tensor's arithmetic does not depend on the rest of the batch,
  * so a tensor's factors are bitwise the same alone and in any batch.  The unit size is chosen by
  * timing candidates on the first call for a batch size class (cached in the context).
@@ -283,6 +290,15 @@ int cpmg_batch_solve(cpmg_ctx* ctx, int count, const cpmg_tensor* Z, const int* 
  * unit_elements < 1, or mode >= N. */
 int cpmg_batch_plan(int N, const int64_t* dims, int R, int64_t unit_elements, int mode, int64_t* units,
                     int64_t max_units, int64_t* n_units, int* nk, int64_t* partial_doubles);
+
+/* Failure-detection test hook of the batched form (the paper has no counterpart).  Every grid
+ * barrier of the batched kernel is a bounded wait: after wait_limit_s seconds (default 2; here
+ * 0 < wait_limit_s <= 60) the waiting CTAs give up, the kernel records the expiry and returns, and
+ * cpmg_batch_solve returns CPMG_TIMEOUT with the context still usable.  unreachable_barrier != 0
+ * makes the first barrier of every launch wait for one CTA more than the launch has, so that wait
+ * always runs out: a test can see the timeout path without faulting or hanging the GPU.  Set it
+ * back to 0 for normal work.  Applies to cpmg_batch_solve calls made after it. */
+int cpmg_debug_config(cpmg_ctx* ctx, double wait_limit_s, int unreachable_barrier);
 
 /* ---- served form ---------------------------------------------------------------------- */
 /* A request server with continuous batching on the context.  Submitted CP-ALS problems (the
@@ -307,6 +323,12 @@ int cpmg_server_submit(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const
 /* CPMG_PENDING while queued or running; CPMG_OK once done, with *result (seconds = latency
  * from submission); the ticket is then released.  CPMG_INVALID_ARG for an unknown ticket. */
 int cpmg_server_poll(cpmg_ctx* ctx, uint64_t ticket, cpmg_result* result);
+/* Cancel a request.  Queued: it leaves the queue at once and its factors are not touched.  Running:
+ * the worker retires it after the launch in flight; its factors hold the last iterate (sorted) and
+ * result f/g are those of that iterate.  Either way the next poll returns CPMG_OK with
+ * result->status = CPMG_CANCELLED (or the request's own status if it finished first).  A finished
+ * request is left as it is.  CPMG_INVALID_ARG for an unknown (or already polled) ticket. */
+int cpmg_server_cancel(cpmg_ctx* ctx, uint64_t ticket);
 /* Block until no request is queued or running (CPMG_PENDING after timeout_s seconds). */
 int cpmg_server_wait(cpmg_ctx* ctx, double timeout_s);
 /* Latency percentiles (submission to completion) and throughput (completions per second since
@@ -321,7 +343,9 @@ int cpmg_server_stats(cpmg_ctx* ctx, double* p50_s, double* p99_s, double* req_p
  * bytes_per_launch = 4 (numel in + numel out).  kind 4 = the launches of the batched kernel in
  * cpmg_batch_solve, with bytes_per_launch the mean over launches of: for every tensor active at
  * the launch, sizeof(z) * prod(I) per MTTKRP pass (N per sweep, N for the g evaluation) plus
- * 16 R sum_n I_n per sweep (float64 factors read and written). */
+ * 16 R sum_n I_n per sweep (float64 factors read and written).  kind 5 = the split-BF16
+ * tensor-core passes over the finest-level tensor (CPMG_PREC_BF16X3 / MIXED_BF16), with
+ * bytes_per_launch = 4 numel + 4 x the product's size. */
 int cpmg_profile_enable(cpmg_ctx* ctx, int enable);
 int cpmg_profile_read(cpmg_ctx* ctx, int kind, double* total_ms, int64_t* launches,
                       double* bytes_per_launch);

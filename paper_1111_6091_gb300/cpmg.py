@@ -25,7 +25,7 @@ MAX_TEST_BLOCKS = 4
 OK, INVALID_ARG, OUT_OF_BUDGET, NOT_CONVERGED, NUMERIC, TIMEOUT, CUDA_ERROR, PENDING, CANCELLED, UNSUPPORTED = range(10)
 F32, F64 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
-PREC_FP32, PREC_FP64, PREC_MIXED, PREC_DF = 0, 1, 2, 3
+PREC_FP32, PREC_FP64, PREC_MIXED, PREC_DF, PREC_BF16X3, PREC_MIXED_BF16 = 0, 1, 2, 3, 4, 5
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcpmg.so")
@@ -97,6 +97,8 @@ _SIGS = {
     "cpmg_batch_solve": (C.c_int, [_P, C.c_int, C.POINTER(cpmg_tensor), C.POINTER(C.c_int), _PP,
                                    C.POINTER(cpmg_opts), C.POINTER(cpmg_result)]),
     "cpmg_server_config": (C.c_int, [_P, C.c_size_t, C.c_int, C.c_int, C.c_int64]),
+    "cpmg_debug_config": (C.c_int, [_P, C.c_double, C.c_int]),
+    "cpmg_server_cancel": (C.c_int, [_P, C.c_uint64]),
     "cpmg_server_submit": (C.c_int, [_P, C.POINTER(cpmg_tensor), C.c_int, _PP, C.POINTER(cpmg_opts),
                                      C.POINTER(C.c_uint64)]),
     "cpmg_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(cpmg_result)]),
@@ -236,6 +238,11 @@ class Context:
     def profile_reset(self):
         _check(lib().cpmg_profile_reset(self.h), "cpmg_profile_reset")
 
+    def debug_config(self, wait_limit_s=2.0, unreachable_barrier=False):
+        """Failure-detection test hook of the batched form (cpmg_debug_config)."""
+        _check(lib().cpmg_debug_config(self.h, float(wait_limit_s), int(bool(unreachable_barrier))),
+               "cpmg_debug_config")
+
 
 # ------------------------------------------------------------------ calls (same names as the ABI)
 def cpmg_mttkrp(ctx, Z, A, mode, precision=PREC_FP32, M=None):
@@ -317,6 +324,9 @@ class Server:
         _check(s, "cpmg_server_poll")
         self._keep.pop(ticket, None)
         return result_dict(r)
+
+    def cancel(self, ticket):
+        _check(lib().cpmg_server_cancel(self.ctx.h, C.c_uint64(ticket)), "cpmg_server_cancel")
 
     def wait(self, timeout_s=600.0):
         return lib().cpmg_server_wait(self.ctx.h, float(timeout_s))

@@ -11,14 +11,15 @@ namespace cpmg {
 constexpr int kDtPhases = 16;  // warps of the mode-0 kernel, each summing every 16th j
 
 // mode 0: block (32 lanes along i) x (16 warps along j), one r per blockIdx.y
-__global__ void __launch_bounds__(32 * kDtPhases) k_dt_mode0(const double* __restrict__ W, int64_t I1, int64_t I2,
+template <typename TW>
+__global__ void __launch_bounds__(32 * kDtPhases) k_dt_mode0(const TW* __restrict__ W, int64_t I1, int64_t I2,
                                                            const double* __restrict__ V, double* out,
                                                            int64_t ld_row, int64_t ld_col) {
   __shared__ double red[kDtPhases][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * 32 + lane;
   const int r = blockIdx.y;
-  const double* Wr = W + (int64_t)r * I1 * I2;
+  const TW* Wr = W + (int64_t)r * I1 * I2;
   const double* Vr = V + (int64_t)r * I2;
   double acc = 0.0;
   if (i < I1) {
@@ -44,7 +45,8 @@ __global__ void __launch_bounds__(32 * kDtPhases) k_dt_mode0(const double* __res
 }
 
 // mode 1: one warp per (j, r), lanes along i, a fixed shuffle tree
-__global__ void __launch_bounds__(256) k_dt_mode1(const double* __restrict__ W, int64_t I1, int64_t I2, int R,
+template <typename TW>
+__global__ void __launch_bounds__(256) k_dt_mode1(const TW* __restrict__ W, int64_t I1, int64_t I2, int R,
                                                   const double* __restrict__ V, double* out, int64_t ld_row,
                                                   int64_t ld_col) {
   const int lane = threadIdx.x & 31;
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(256) k_dt_mode1(const double* __restrict__ W, 
   if (item >= I2 * R) return;
   const int64_t j = item % I2;
   const int r = (int)(item / I2);
-  const double* col = W + (int64_t)r * I1 * I2 + I1 * j;
+  const TW* col = W + (int64_t)r * I1 * I2 + I1 * j;
   const double* Vr = V + (int64_t)r * I1;
   double acc = 0.0;
   int64_t i = lane;
@@ -71,7 +73,9 @@ __global__ void __launch_bounds__(256) k_dt_mode1(const double* __restrict__ W, 
 // ------------------------------------------------------------------ W = X C (one pass over X)
 constexpr int kWThreads = 128;
 constexpr int kWTile = 256;    // columns of C staged in shared memory at a time
-constexpr int kWUnroll = 8;    // columns of X whose loads are in flight together
+// columns of X whose loads are in flight together: FP32 keeps 16 (the bytes in flight per SM set
+// the streaming rate); the float-pair and float64 accumulators leave registers for 8
+constexpr int w_unroll(int prec) { return prec == P_FP32 ? 16 : 8; }
 
 // accumulation per precision: FP32 fma; float pairs (the product's error and the TwoSum error of
 // the running sum go to the low word, folded back after every group of columns); float64 fma
@@ -166,12 +170,13 @@ __global__ void __launch_bounds__(kWThreads) k_dt_w(const TZ* __restrict__ X, in
     if (!live) continue;
     const TZ* xp = X + p0 + P * k0;
     int kk = 0;
-    for (; kk + kWUnroll <= kt; kk += kWUnroll) {
-      WVec<TZ, VW> x[kWUnroll];
+    constexpr int U = w_unroll(PREC);
+    for (; kk + U <= kt; kk += U) {
+      WVec<TZ, VW> x[U];
 #pragma unroll
-      for (int u = 0; u < kWUnroll; ++u) x[u].load(xp + P * (kk + u));
+      for (int u = 0; u < U; ++u) x[u].load(xp + P * (kk + u));
 #pragma unroll
-      for (int u = 0; u < kWUnroll; ++u) {
+      for (int u = 0; u < U; ++u) {
         const S* c = cs + (kk + u) * RP;
 #pragma unroll
         for (int r = 0; r < RP; ++r) {
@@ -239,8 +244,9 @@ int launch_dt_w(const void* X, int zdtype, int64_t P, int64_t K, int R, const do
                 : vw == 2 ? launch_w_rp<float, P_FP32, 2>(x, P, K, R, C, W, st)
                           : launch_w_rp<float, P_FP32, 1>(x, P, K, R, C, W, st);
         break;
-      case P_DF:
-        vw >= 2 ? launch_w_rp<float, P_DF, 2>(x, P, K, R, C, W, st) : launch_w_rp<float, P_DF, 1>(x, P, K, R, C, W, st);
+      case P_DF:  // two rows of float-pair accumulators fit the registers up to R = 8
+        (vw >= 2 && R <= 8) ? launch_w_rp<float, P_DF, 2>(x, P, K, R, C, W, st)
+                            : launch_w_rp<float, P_DF, 1>(x, P, K, R, C, W, st);
         break;
       default:
         vw >= 2 ? launch_w_rp<float, P_FP64, 2>(x, P, K, R, C, W, st) : launch_w_rp<float, P_FP64, 1>(x, P, K, R, C, W, st);
@@ -250,16 +256,76 @@ int launch_dt_w(const void* X, int zdtype, int64_t P, int64_t K, int R, const do
   return CPMG_OK;
 }
 
-int launch_dt_contract(const double* W, int64_t I1, int64_t I2, int R, const double* V, int mode, double* out,
+// mode 3 from V = Z x_1 A^(1)^T (R x I2 x I3, r fastest): out(k, r) = sum_j V(r, j, k) U(j, r).
+// Thread (k, r), r fastest, so a warp reads whole r-runs of V; j in increasing order.
+__global__ void __launch_bounds__(256) k_dt_vmode(const float* __restrict__ V, int64_t I2, int64_t I3, int R,
+                                                  const double* __restrict__ U, double* out, int64_t ld_row,
+                                                  int64_t ld_col) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= I3 * R) return;
+  const int r = (int)(t % R);
+  const int64_t k = t / R;
+  const float* v = V + (int64_t)R * I2 * k + r;
+  const double* u = U + (int64_t)r * I2;
+  double acc = 0.0;
+  int64_t j = 0;
+  for (; j + 3 < I2; j += 4) {
+    const double a0 = v[R * j], a1 = v[R * (j + 1)], a2 = v[R * (j + 2)], a3 = v[R * (j + 3)];
+    acc = fma(a0, u[j], acc);
+    acc = fma(a1, u[j + 1], acc);
+    acc = fma(a2, u[j + 2], acc);
+    acc = fma(a3, u[j + 3], acc);
+  }
+  for (; j < I2; ++j) acc = fma((double)v[R * j], u[j], acc);
+  out[k * ld_row + (int64_t)r * ld_col] = acc;
+}
+
+template <typename TW>
+static int dt_contract(const TW* W, int64_t I1, int64_t I2, int R, const double* V, int mode, double* out,
                        int64_t ld_row, int64_t ld_col, cudaStream_t st) {
   if (I1 < 1 || I2 < 1 || R < 1 || (mode != 0 && mode != 1)) return CPMG_INVALID_ARG;
   if (mode == 0) {
     const dim3 grid((unsigned)((I1 + 31) / 32), (unsigned)R);
-    k_dt_mode0<<<grid, 32 * kDtPhases, 0, st>>>(W, I1, I2, V, out, ld_row, ld_col);
+    k_dt_mode0<TW><<<grid, 32 * kDtPhases, 0, st>>>(W, I1, I2, V, out, ld_row, ld_col);
   } else {
     const int64_t items = I2 * R;
-    k_dt_mode1<<<(unsigned)((items + 7) / 8), 256, 0, st>>>(W, I1, I2, R, V, out, ld_row, ld_col);
+    k_dt_mode1<TW><<<(unsigned)((items + 7) / 8), 256, 0, st>>>(W, I1, I2, R, V, out, ld_row, ld_col);
   }
+  CPMG_CUDA_TRY(cudaGetLastError());
+  return CPMG_OK;
+}
+
+int launch_dt_contract(const double* W, int64_t I1, int64_t I2, int R, const double* V, int mode, double* out,
+                       int64_t ld_row, int64_t ld_col, cudaStream_t st) {
+  return dt_contract(W, I1, I2, R, V, mode, out, ld_row, ld_col, st);
+}
+
+int launch_dt_contract_f(const float* W, int64_t I1, int64_t I2, int R, const double* V, int mode, double* out,
+                         int64_t ld_row, int64_t ld_col, cudaStream_t st) {
+  return dt_contract(W, I1, I2, R, V, mode, out, ld_row, ld_col, st);
+}
+
+int launch_dt_vmode(const float* V, int64_t I2, int64_t I3, int R, const double* U, double* out, int64_t ld_row,
+                    int64_t ld_col, cudaStream_t st) {
+  if (I2 < 1 || I3 < 1 || R < 1) return CPMG_INVALID_ARG;
+  const int64_t n = I3 * R;
+  k_dt_vmode<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, I2, I3, R, U, out, ld_row, ld_col);
+  CPMG_CUDA_TRY(cudaGetLastError());
+  return CPMG_OK;
+}
+
+// transposed copy: dst (R x I, column-major) = src^T (src: I x R column-major)
+__global__ void k_transpose_d(const double* __restrict__ src, int64_t I, int R, double* __restrict__ dst) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= I * R) return;
+  const int r = (int)(t % R);
+  const int64_t i = t / R;
+  dst[r + (int64_t)R * i] = src[i + I * r];
+}
+
+int launch_transpose_d(const double* src, int64_t I, int R, double* dst, cudaStream_t st) {
+  const int64_t n = I * R;
+  k_transpose_d<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, I, R, dst);
   CPMG_CUDA_TRY(cudaGetLastError());
   return CPMG_OK;
 }

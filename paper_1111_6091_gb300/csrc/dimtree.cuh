@@ -19,6 +19,18 @@ namespace cpmg {
 // W: I1 x I2 x R column-major float64.  Summation orders depend only on the sizes.
 int launch_dt_contract(const double* W, int64_t I1, int64_t I2, int R, const double* V, int mode, double* out,
                        int64_t ld_row, int64_t ld_col, cudaStream_t st);
+// The same with a float W (the tensor-core products of the split-BF16 path write float).
+int launch_dt_contract_f(const float* W, int64_t I1, int64_t I2, int R, const double* V, int mode, double* out,
+                         int64_t ld_row, int64_t ld_col, cudaStream_t st);
+
+// Mode 3 from V = Z x_1 A^(1)^T, an R x I2 x I3 float array with r fastest (the tensor-core mode-1
+// product's layout): out(k, r) at out[k * ld_row + r * ld_col] = sum_j V(r, j, k) U(j, r), U the
+// I2 x R float64 factor A^(2).  Summation over j in increasing order.
+int launch_dt_vmode(const float* V, int64_t I2, int64_t I3, int R, const double* U, double* out, int64_t ld_row,
+                    int64_t ld_col, cudaStream_t st);
+
+// dst (R x I column-major) = src^T for an I x R column-major float64 factor.
+int launch_transpose_d(const double* src, int64_t I, int R, double* dst, cudaStream_t st);
 
 // W(p, r) = sum_k X(p, k) C(k, r) for the P x K column-major matricization X of a tensor (float or
 // float64 elements, `zdtype`) and a float64 K x R factor C, written as float64 P x R column-major.

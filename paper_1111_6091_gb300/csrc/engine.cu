@@ -54,9 +54,9 @@ struct cpmg_ctx {
   bool profile = false;
   std::vector<ProfEvents> pending;
   std::vector<ProfEvents> pool;
-  double prof_ms[5] = {0, 0, 0, 0, 0};
-  int64_t prof_launches[5] = {0, 0, 0, 0, 0};
-  double prof_bytes[5] = {0, 0, 0, 0, 0};
+  double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+  int64_t prof_launches[6] = {0, 0, 0, 0, 0, 0};
+  double prof_bytes[6] = {0, 0, 0, 0, 0, 0};
   int64_t launches = 0;
   const void* prof_Z = nullptr;  // tensor whose MTTKRPs are profiled (the finest level)
   bool capturing = false;        // a CUDA graph capture is open on `stream`
@@ -272,6 +272,7 @@ namespace cpmg {
 int ctx_profile_events(cpmg_ctx* c, int kind, double bytes, cudaEvent_t* e0, cudaEvent_t* e1) {
   *e0 = *e1 = nullptr;
   if (!c->profile) return CPMG_OK;
+  if (c->pending.size() > 512) CPMG_TRY(profile_collect(c));  // recycle read-out event pairs
   return prof_events(c, kind, bytes, e0, e1);
 }
 }  // namespace cpmg
@@ -342,6 +343,11 @@ struct Level {
   double* buf = nullptr;   // backing store of F, H
   double* M = nullptr;     // I_max x R work
   double* W = nullptr;     // I_1 x I_2 x R partial MTTKRP of the dimension tree (third order)
+  // split-BF16 tensor-core passes (float third-order levels of the dimension tree)
+  float* Wf = nullptr;     // Z x_3 A^(3)^T, I_1 I_2 x R
+  float* Vf = nullptr;     // Z x_1 A^(1)^T, R x I_2 x I_3
+  double* AT = nullptr;    // a factor transposed (R x I_max), the tensor-core B operand
+  void* tcs = nullptr;     // split-BF16 copy of AT
   double* twork = nullptr; // transform work (2 * Ic_max)
   double* blk = nullptr;   // block norms / weights (3 * (nt+1))
   bool coarsest() const {
@@ -353,6 +359,9 @@ struct Level {
 
 // Third-order levels keep the dimension tree's W when it is small next to a pass over Z.
 static bool dt_worth(const Shape& s, int R) { return s.N == 3 && s.dims[2] > 6 * (int64_t)R; }
+static bool uses_bf16(const cpmg_opts* o) {
+  return o->precision == CPMG_PREC_BF16X3 || o->precision == CPMG_PREC_MIXED_BF16;
+}
 
 constexpr int kBlkStride = 40;  // doubles of LS-weight bookkeeping per mode (Level::blk)
 
@@ -369,6 +378,19 @@ struct cpmg_hier {
   void* tcs = nullptr;     // split R-hat operand of the tensor-core restriction
   GraphCache graphs;
 };
+
+// Buffers of the split-BF16 tensor-core passes: the two products W = Z x_3 A^(3)^T and
+// V = Z x_1 A^(1)^T (float), the transposed factor they contract with, and its split copy.
+static int tc_level_alloc(cpmg_ctx* c, Level& L, int R) {
+  if (L.Wf || L.dtype != CPMG_F32 || !dt_worth(L.s, R) || !ttm_tc_supported(L.s, CPMG_F32, 0, R) ||
+      !ttm_tc_supported(L.s, CPMG_F32, 2, R))
+    return CPMG_OK;
+  const int64_t P = L.s.dims[0] * L.s.dims[1], imax = std::max(L.s.dims[0], L.s.dims[2]);
+  CPMG_TRY(dalloc(c, reinterpret_cast<void**>(&L.Wf), sizeof(float) * (size_t)P * R));
+  CPMG_TRY(dalloc(c, reinterpret_cast<void**>(&L.Vf), sizeof(float) * (size_t)R * L.s.dims[1] * L.s.dims[2]));
+  CPMG_TRY(dalloc_t(c, &L.AT, (size_t)R * imax));
+  return dalloc(c, &L.tcs, ttm_tc_scratch_bytes(imax));
+}
 
 static int level_alloc(cpmg_ctx* c, Level& L, int R, int nt) {
   const int N = L.s.N;
@@ -409,6 +431,10 @@ static void level_free(cpmg_ctx* c, Level& L) {
   dfree(c, L.buf);
   dfree(c, L.M);
   dfree(c, L.W);
+  dfree(c, L.Wf);
+  dfree(c, L.Vf);
+  dfree(c, L.AT);
+  dfree(c, L.tcs);
   dfree(c, L.twork);
   dfree(c, L.blk);
   dfree(c, L.Zown);
@@ -474,6 +500,7 @@ static int hier_build(cpmg_ctx* c, const Shape& s0, int dtype, int R, const cpmg
   int st = CPMG_OK;
   for (size_t l = 0; l < h->L.size() && st == CPMG_OK; ++l) {
     st = level_alloc(c, h->L[l], R, h->nt);
+    if (st == CPMG_OK && uses_bf16(o)) st = tc_level_alloc(c, h->L[l], R);
     if (st == CPMG_OK && l > 0) {
       const size_t esz = dtype == CPMG_F64 ? 8 : 4;
       st = dalloc(c, &h->L[l].Zown, (size_t)h->L[l].s.numel() * esz);
@@ -521,6 +548,8 @@ struct Solver {
       case CPMG_PREC_FP32: return P_FP32;
       case CPMG_PREC_FP64: return P_FP64;
       case CPMG_PREC_DF: return hi;
+      case CPMG_PREC_BF16X3: return dtype == CPMG_F32 ? P_BF16 : P_FP64;
+      case CPMG_PREC_MIXED_BF16: return refined ? hi : (dtype == CPMG_F32 ? P_BF16 : P_FP32);
       // Once refined, every level is: FP32 rounding on a coarse level would otherwise enter
       // each FAS correction at ~1e-7 relative, independent of the fine residual.
       default: return refined ? hi : P_FP32;
@@ -556,11 +585,48 @@ static int dt_form_w(Solver& S, const Level& L, const FactorSet& f, int prec) {
   return CPMG_OK;
 }
 
+// ---------------------------------------------------------------- split BF16 on tensor cores
+// Both passes of the dimension tree as tcgen05 mode products (the restriction's kernel, Ic = R):
+// W = Z x_3 A^(3)^T gives modes 1 and 2, V = Z x_1 A^(1)^T gives mode 3.  P_BF16 anywhere else
+// (a level without the tree, a float64 tensor) runs the FP32 kernels.
+static bool use_tc(const Solver& S, const Level& L, int R) { return L.Wf && use_dt(S, L, R); }
+static int plain_prec(int prec) { return prec == P_BF16 ? P_FP32 : prec; }
+
+static int tc_product(Solver& S, const Level& L, const FactorSet& f, int mode, float* Y) {
+  cpmg_ctx* c = S.c;
+  const int64_t In = L.s.dims[mode];
+  CPMG_TRY(launch_transpose_d(f.A[mode], In, f.R, L.AT, S.st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profile && L.Z == c->prof_Z) {
+    // algorithmic traffic: Z once, the product written once
+    const double out = mode == 0 ? (double)f.R * L.s.dims[1] * L.s.dims[2] : (double)f.R * L.s.dims[0] * L.s.dims[1];
+    CPMG_TRY(prof_events(c, 5, 4.0 * (double)L.s.numel() + 4.0 * out, &e0, &e1));
+  }
+  CPMG_TRY(ttm_mode_tc(L.s, static_cast<const float*>(L.Z), mode, L.AT, f.R, Y, L.tcs, c->dstatus + 1, e0, e1,
+                       c->capturing, S.st));
+  c->launches += 3;
+  return CPMG_OK;
+}
+
 // The N products M^(n) = Z_(n) Phi^(n) at one point f (all modes, no update between them),
 // handed in mode order to use(n, M) with M = L.M (overwritten by the next mode).  With the
 // dimension tree this streams Z twice instead of N times.
 template <typename Fn>
 static int mttkrp_all(Solver& S, const Level& L, const FactorSet& f, int prec, Fn&& use) {
+  if (prec == P_BF16 && use_tc(S, L, f.R)) {
+    CPMG_TRY(tc_product(S, L, f, 2, L.Wf));
+    for (int n = 0; n < 2; ++n) {
+      CPMG_TRY(launch_dt_contract_f(L.Wf, L.s.dims[0], L.s.dims[1], f.R, n == 0 ? f.A[1] : f.A[0], n, L.M, 1,
+                                    L.s.dims[n], S.st));
+      S.c->launches += 1;
+      CPMG_TRY(use(n, L.M));
+    }
+    CPMG_TRY(tc_product(S, L, f, 0, L.Vf));
+    CPMG_TRY(launch_dt_vmode(L.Vf, L.s.dims[1], L.s.dims[2], f.R, f.A[1], L.M, 1, L.s.dims[2], S.st));
+    S.c->launches += 1;
+    return use(2, L.M);
+  }
+  prec = plain_prec(prec);
   if (use_dt(S, L, f.R)) {
     CPMG_TRY(dt_form_w(S, L, f, prec));
     for (int n = 0; n < 2; ++n) {
@@ -586,26 +652,47 @@ static int mttkrp_all(Solver& S, const Level& L, const FactorSet& f, int prec, F
 static int sweep_modes(Solver& S, const Level& L, FactorSet& f, int prec, int kind, bool hasF,
                        bool normalize_last) {
   const int gs = kind == 1 ? S.o.gs_sweeps : 0;
+  // products taken outside the MTTKRP kernels go to the fused update kernel as one float64
+  // partial row per output row
+  MttkrpPlan q;
+  q.mode = 1;
+  q.nseg = 1;
+  q.C = 1;
+  q.nw = 1;
+  q.RP = f.R;
+  q.SEG = 1;
+  q.part_elem = 8;
+  MttkrpScratch w;
+  w.partial = S.c->mt_partial;
+  w.tables = S.c->mt_tables;
+  double* rows = static_cast<double*>(S.c->mt_partial);
+  auto update = [&](int n, bool norm) -> int {
+    S.c->launches += 1;
+    return launch_finish_update(q, w, f, n, kind, hasF ? L.F[n] : nullptr, gs, nullptr, S.c->gscratch,
+                                S.c->dstatus + 2, S.c->dstatus, S.st, norm);
+  };
+  if (prec == P_BF16 && use_tc(S, L, f.R)) {
+    CPMG_TRY(tc_product(S, L, f, 2, L.Wf));
+    for (int n = 0; n < 2; ++n) {
+      CPMG_TRY(launch_dt_contract_f(L.Wf, L.s.dims[0], L.s.dims[1], f.R, n == 0 ? f.A[1] : f.A[0], n, rows, f.R, 1,
+                                    S.st));
+      S.c->launches += 1;
+      CPMG_TRY(update(n, false));
+    }
+    // mode 3 needs the updated A^(1) and A^(2): V = Z x_1 A^(1)^T, then the contraction with A^(2)
+    CPMG_TRY(tc_product(S, L, f, 0, L.Vf));
+    CPMG_TRY(launch_dt_vmode(L.Vf, L.s.dims[1], L.s.dims[2], f.R, f.A[1], rows, f.R, 1, S.st));
+    S.c->launches += 1;
+    return update(2, normalize_last);
+  }
+  prec = plain_prec(prec);
   if (use_dt(S, L, f.R)) {
     CPMG_TRY(dt_form_w(S, L, f, prec));
-    // the products go to the fused update kernel as one float64 partial row per output row
-    MttkrpPlan q;
-    q.mode = 1;
-    q.nseg = 1;
-    q.C = 1;
-    q.nw = 1;
-    q.RP = f.R;
-    q.SEG = 1;
-    q.part_elem = 8;
-    MttkrpScratch w;
-    w.partial = S.c->mt_partial;
-    w.tables = S.c->mt_tables;
     for (int n = 0; n < 2; ++n) {
-      CPMG_TRY(launch_dt_contract(L.W, L.s.dims[0], L.s.dims[1], f.R, n == 0 ? f.A[1] : f.A[0], n,
-                                  static_cast<double*>(S.c->mt_partial), f.R, 1, S.st));
-      CPMG_TRY(launch_finish_update(q, w, f, n, kind, hasF ? L.F[n] : nullptr, gs, nullptr, S.c->gscratch,
-                                    S.c->dstatus + 2, S.c->dstatus, S.st, false));
-      S.c->launches += 2;
+      CPMG_TRY(launch_dt_contract(L.W, L.s.dims[0], L.s.dims[1], f.R, n == 0 ? f.A[1] : f.A[0], n, rows, f.R, 1,
+                                  S.st));
+      S.c->launches += 1;
+      CPMG_TRY(update(n, false));
     }
     return run_mttkrp_k(S.c, L.s, L.Z, L.dtype, f, 2, prec, nullptr, kind, hasF ? L.F[2] : nullptr, gs,
                         normalize_last);
@@ -621,7 +708,7 @@ static int als_sweep(Solver& S, const Level& L, int lvl, FactorSet& f) {
   const int prec = S.prec_for(lvl, L.dtype);
   // the last mode's update also normalizes (Eq. ALSnorm) in its final block
   CPMG_TRY(sweep_modes(S, L, f, prec, 0, false, true));
-  if (lvl == 0 && prec != P_FP32) S.refine_sweeps++;
+  if (lvl == 0 && prec != P_FP32 && prec != P_BF16) S.refine_sweeps++;
   return CPMG_OK;
 }
 
@@ -639,7 +726,7 @@ static int relax_bngs(Solver& S, const Level& L, int lvl, FactorSet& f, bool has
   const int prec = S.prec_for(lvl, L.dtype);
   for (int it = 0; it < iters; ++it) {
     CPMG_TRY(sweep_modes(S, L, f, prec, 1, hasF, false));
-    if (lvl == 0 && prec != P_FP32) S.refine_sweeps++;
+    if (lvl == 0 && prec != P_FP32 && prec != P_BF16) S.refine_sweeps++;
     if (top) {
       CPMG_TRY(launch_normalize(f, S.st));
       CPMG_TRY(launch_sort(f, S.sortbuf, S.st));
@@ -688,9 +775,11 @@ static int eval_g(Solver& S, const Level& L, FactorSet& f, double* g, double* mn
 // FP32 floor, estimated as eps_32 ||M|| / ||Z|| (the size of one FP32 rounding of the
 // MTTKRP seen through Eq. gradConv), or after 20 checks without a new smallest g.
 static void maybe_switch(Solver& S, double g, double mnorm, double /*g_prev*/) {
-  if (S.policy != CPMG_PREC_MIXED || S.refined) return;
+  if ((S.policy != CPMG_PREC_MIXED && S.policy != CPMG_PREC_MIXED_BF16) || S.refined) return;
   const double K = S.o.mixed_switch > 0 ? S.o.mixed_switch : 4.0;
-  const double floor_est = K * 5.960464477539063e-08 * mnorm / S.znorm;
+  // one rounding of the sweep's products: 2^-24 in FP32, about 2^-16 for split BF16
+  const double u = S.policy == CPMG_PREC_MIXED_BF16 ? 1.52587890625e-05 : 5.960464477539063e-08;
+  const double floor_est = K * u * mnorm / S.znorm;
   if (S.g_best < 0 || g < S.g_best) {
     S.g_best = g;
     S.stall = 0;
@@ -859,7 +948,7 @@ static int build_operators(Solver& S, cpmg_hier* h, int lvl, bool first) {
     for (int k = 0; k < nb; ++k) U[k] = blocks[k]->A[n];
     double* b = L.blk + kBlkStride * n;
     // a gradient at the rounding level of the MTTKRP that produced it counts as zero
-    const double tau = prec == P_FP32 ? 1e-5 : 1e-12;
+    const double tau = prec == P_BF16 ? 1e-4 : prec == P_FP32 ? 1e-5 : 1e-12;
     CPMG_TRY(launch_block_weights(nb, b, b + 8, b + 24, tau, b + 16, S.st));
     CPMG_TRY(launch_interp(L.s.dims[n], R, nb, U, b + 16, L.Pw[n], S.st));
     CPMG_TRY(launch_transform(L.s.dims[n], L.Pw[n], L.Rhat[n], L.twork, S.st));
@@ -1038,7 +1127,7 @@ static Solver make_solver(cpmg_ctx* c, const cpmg_opts* o) {
 
 static int check_opts(const cpmg_opts* o) {
   if (!o) return CPMG_INVALID_ARG;
-  if (o->precision < 0 || o->precision > 3) return CPMG_INVALID_ARG;
+  if (o->precision < 0 || o->precision > 5) return CPMG_INVALID_ARG;
   if (o->n_t < 0 || o->n_t > CPMG_MAX_TEST_BLOCKS) return CPMG_INVALID_ARG;
   if (o->gs_sweeps < 0 || o->nu1 < 0 || o->nu2 < 0 || o->nuc < 0) return CPMG_INVALID_ARG;
   return CPMG_OK;
@@ -1172,7 +1261,7 @@ int cpmg_profile_enable(cpmg_ctx* c, int enable) {
 }
 
 int cpmg_profile_read(cpmg_ctx* c, int kind, double* total_ms, int64_t* launches, double* bytes) {
-  if (!c || kind < 0 || kind > 4) return CPMG_INVALID_ARG;
+  if (!c || kind < 0 || kind > 5) return CPMG_INVALID_ARG;
   CPMG_TRY(profile_collect(c));
   if (total_ms) *total_ms = c->prof_ms[kind];
   if (launches) *launches = c->prof_launches[kind];
@@ -1183,7 +1272,7 @@ int cpmg_profile_read(cpmg_ctx* c, int kind, double* total_ms, int64_t* launches
 int cpmg_profile_reset(cpmg_ctx* c) {
   if (!c) return CPMG_INVALID_ARG;
   CPMG_TRY(profile_collect(c));
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     c->prof_ms[k] = 0;
     c->prof_launches[k] = 0;
     c->prof_bytes[k] = 0;
@@ -1314,6 +1403,7 @@ int cp_als_sweep(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A, int
   if (st == CPMG_OK) st = dalloc_t(c, &L.M, (size_t)imax * R);
   if (st == CPMG_OK && opts->dimension_tree && dt_worth(L.s, R))
     st = dalloc_t(c, &L.W, (size_t)L.s.dims[0] * L.s.dims[1] * R);
+  if (st == CPMG_OK && opts->dimension_tree && uses_bf16(opts)) st = tc_level_alloc(c, L, R);
   if (st == CPMG_OK) st = dalloc_t(c, &S.sortbuf, fs_doubles(Z->N, R, L.s.dims));
   if (st == CPMG_OK) st = factors_in(c, Z->mem, A, fs);
   double z2 = 0, fv = 0, g = -1, gprev = -1, mn = 0;
@@ -1367,6 +1457,10 @@ int cp_als_sweep(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A, int
   if (st == CPMG_OK && (!std::isfinite(fv) || !std::isfinite(g))) st = CPMG_NUMERIC;
   if (st == CPMG_OK && opts->check_every != 0 && !conv && !(g < opts->tol)) st = CPMG_NOT_CONVERGED;
   if (res) res->status = st;
+  dfree(c, L.Wf);
+  dfree(c, L.Vf);
+  dfree(c, L.AT);
+  dfree(c, L.tcs);
   dfree(c, L.W);
   dfree(c, L.M);
   dfree(c, S.sortbuf);

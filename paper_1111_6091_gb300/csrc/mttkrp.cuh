@@ -4,7 +4,9 @@
 
 namespace cpmg {
 
-enum Prec { P_FP32 = 0, P_FP64 = 1, P_DF = 3 };
+// P_BF16 (split BF16 on tensor cores) is the engine's, never a plan's: the MTTKRP kernels here run
+// P_FP32 in its place.
+enum Prec { P_FP32 = 0, P_FP64 = 1, P_DF = 3, P_BF16 = 4 };
 
 // Launch geometry and table layout for one (shape, mode, precision).
 struct MttkrpPlan {
