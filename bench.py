@@ -1,22 +1,23 @@
 #!/usr/bin/env python3
-"""Benchmark: time-to-tolerance of the multilevel CP solver on one GPU.
+"""Benchmark: time-to-tolerance of the batched CP-ALS form on one GPU.
 
-Workload (one step): the 100x100x100 float32 tensor of rank 5 whose factor columns have
-pairwise congruence 0.9, with 1% homoscedastic and 5% heteroscedastic noise (seeded
-synthetic data), decomposed by the "Multilevel" solver (CP-AMG-mult setup cycles, then
-CP-FAS solve cycles with the one-time rebuild, then plain ALS if stagnation persists)
-from a fixed N(0,1) start until g < 1e-8 (Eq. gradConv), levels 100/50/25/13, MIXED
-precision (FP32 sweeps, float64-accurate sweeps near the FP32 floor).
+Workload (one step): 512 independent dense tensors (order 3 or 4 with probability 1/2, mode sizes
+uniform in [16, 128] ([16, 48] for order 4), rank uniform in 2..8, factor columns with pairwise
+congruence uniform in [0.5, 0.95], 1% noise; seeded synthetic float32 data) decomposed by CP-ALS
+(Section 3) from fixed N(0,1) starts until every tensor's g of Eq. gradConv is below 1e-8, or it
+has run the 1e4 ALS iterations of Section 6.1, all in one cooperative persistent kernel per check
+interval, MIXED precision (FP32 sweeps, float64-accurate sweeps near the FP32 floor; float64 Grams,
+solves and g).  `value` is the seconds one step takes with the tensors resident in HBM (1.3 GB,
+larger than the 126 MB L2); the batched kernel's launches are timed with CUDA events inside the
+timed steps (roofline).  `e2e` repeats the step through the same C ABI call with pinned host
+buffers, the copies inside the call.  The same batch in plain FP64 on the GPU, and as a loop of
+per-tensor calls, is reported beside it.
 
-Timing: W untimed steps, then K steps each bracketed by CUDA events on the library's
-stream, with a 512 MB write between steps to flush the 126 MB L2 (the tensor is 4 MB).
-The finest-level MTTKRP launches inside the timed steps are timed with events by the
-library (roofline).  The end-to-end number repeats the solve through the same C ABI call
-with pinned host buffers, the copies inside the timed region.  A second measurement
-times the FP32 MTTKRP of the 400x400x400 rank-10 tensor (256 MB, larger than L2) against
-the measured HBM peak.
+Further measurements on the same line: the 100^3 rank-5 multilevel solve (Section 6.1 driver), the
+400^3 rank-10 sweep and its MTTKRP against the measured HBM peak, the tensor-core restriction, the
+served request stream and the paper's dense test tensor.
 
-``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload instead.
 """
 from __future__ import annotations
 
@@ -34,11 +35,15 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "time-to-tol (rel err 1e-8)"
+BATCH_COUNT, BATCH_TOL, BATCH_MAX_IT, BATCH_CHECK = 512, 1e-8, 10000, 8
+WORKLOAD = ("batched CP-ALS: 512 dense tensors, order 3/4, sizes U[16,128] (U[16,48] for order 4), "
+            "R U{2..8}, congruence U[0.5,0.95], 1% noise, fp32, g<1e-8, at most 1e4 sweeps")
+
+# the 100^3 rank-5 multilevel workload (congruence 0.9, 1% + 5% noise, levels 100/50/25/13)
 DIMS, RANK, CONG, ETA1, ETA2, SEED = (100, 100, 100), 5, 0.9, 0.01, 0.05, 0
 COARSEST = (13, 13, 13)
 TOL = 1e-8
-METRIC = "time-to-tol (rel err 1e-8)"
-WORKLOAD = "dense 100x100x100 fp32, R=5, congruence 0.9, noise 1%+5%, multilevel 4 levels, g<1e-8"
 
 
 def problem():
@@ -48,9 +53,12 @@ def problem():
 
 
 def config(extra=None):
-    c = {"workload": WORKLOAD, "dims": list(DIMS), "rank": RANK, "congruence": CONG,
-         "noise": [ETA1, ETA2], "tol": TOL, "solver": "multilevel (setup + FAS + ALS fallback)",
-         "precision": "mixed fp32 / float-pair", "l2": "flushed between steps (512 MB write)"}
+    c = {"workload": WORKLOAD, "count": BATCH_COUNT, "order": [3, 4], "dims": "U[16,128] (order 4: U[16,48])",
+         "rank": "U{2..8}", "congruence": "U[0.5,0.95]", "noise": 0.01, "tol": BATCH_TOL,
+         "max_sweeps": BATCH_MAX_IT, "check_every": BATCH_CHECK,
+         "solver": "CP-ALS (Section 3), one cooperative persistent kernel per check interval",
+         "precision": "mixed fp32 / float-pair sweeps, float64 Grams, solves and g",
+         "l2": "inputs larger than L2 (1.3 GB resident)"}
     if extra:
         c.update(extra)
     return c
@@ -67,11 +75,44 @@ def peaks():
 
 # ------------------------------------------------------------------ oracle (CPU)
 def oracle_solve(p):
+    """The FP64 oracle's multilevel solve (Section 6.1 driver) of the 100^3 workload."""
     from oracle import multigrid as MG
     o = MG.Options(coarsest=COARSEST, tol=TOL, als_fallback=True)
     t = time.perf_counter()
     r = MG.multilevel(p.Z.astype(np.float64), p.A0, p.tfms, o)
     return time.perf_counter() - t, r
+
+
+def oracle_batch_tensor(p):
+    """The FP64 oracle's ALS on one tensor of the batch, from the same start as the GPU, to g < 1e-8
+    checked every 8 iterations (as the batched kernel checks), at most 1e4 iterations.  Returns
+    (seconds, factors, iterations, g)."""
+    from oracle import als as ALS, tensor as T
+    Z64 = p.Z.astype(np.float64)
+    t = time.perf_counter()
+    A, it, g = p.A0, 0, T.g_value(Z64, p.A0)
+    while it < BATCH_MAX_IT and g >= BATCH_TOL:
+        A, _ = ALS.als(Z64, A, BATCH_CHECK, sort_at_end=False)
+        it += BATCH_CHECK
+        g = T.g_value(Z64, A)
+    A = ALS.sort_components(A)
+    return time.perf_counter() - t, A, it, g
+
+
+def oracle_sweep_cost(probs, count=16, sweeps=4):
+    """Seconds per (mode x element) of one oracle ALS iteration, measured on the first `count`
+    tensors of the batch (`sweeps` iterations each): the oracle's cost of a sweep is N MTTKRPs,
+    each a pass over the tensor."""
+    from oracle import als as ALS
+    t = time.perf_counter()
+    work = 0
+    for p in probs[:count]:
+        Z64 = p.Z.astype(np.float64)
+        A = p.A0
+        for _ in range(sweeps):
+            A = ALS.als_sweep(Z64, A)
+        work += sweeps * p.Z.ndim * p.Z.size
+    return (time.perf_counter() - t) / work
 
 
 def blas_threads():
@@ -83,29 +124,37 @@ def blas_threads():
         return os.cpu_count() or 1
 
 
+REF_SAMPLE = 4     # tensors the oracle solves per reference step
+REF_POOL = 64      # the reference steps cycle through the first 64 tensors of the batch
+
+
 def run_reference(args):
+    """The oracle arm: each step, the FP64 NumPy oracle solves REF_SAMPLE tensors of the batch to
+    tolerance (the same problems and starts as the GPU); the step's value is their total time
+    scaled to the 512 tensors of the workload."""
     _, rank, _ = rank_env()
     if rank != 0:
         return
-    p = problem()
-    for _ in range(min(args.warmup, 1)):
-        oracle_solve(p)
-    times = []
-    r = None
-    for _ in range(args.steps):
-        dt, r = oracle_solve(p)
-        times.append(dt)
-    v = statistics.mean(times)
+    probs = batch_problems(REF_POOL)
+
+    def one(step):
+        idx = [(REF_SAMPLE * step + j) % REF_POOL for j in range(REF_SAMPLE)]
+        return sum(oracle_batch_tensor(probs[i])[0] for i in idx) * BATCH_COUNT / REF_SAMPLE
+
+    for w in range(min(args.warmup, 1)):
+        one(REF_POOL // REF_SAMPLE - 1 - w)
+    vals = [one(s) for s in range(args.steps)]
+    v = statistics.mean(vals)
+    sample = (f"per step, the FP64 NumPy oracle's ALS solves {REF_SAMPLE} tensors of the batch (cycling through "
+              f"the first {REF_POOL}) to g<1e-8; value = their time x {BATCH_COUNT}/{REF_SAMPLE}")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * v,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config(),
-        "cpu_baseline": {"value": v, "unit": "s", "cores": blas_threads(), "kind": "oracle",
-                         "sample": "full solve of the workload by the FP64 NumPy oracle"},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": blas_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "oracle_cycles": {"setup": r.setup_cycles, "solve": r.solve_cycles,
-                          "als": getattr(r, "als_iters", 0), "converged": bool(r.converged)},
+        "step_values": vals,
     }
     print(json.dumps(line), flush=True)
 
@@ -177,6 +226,10 @@ def max_over_ranks(x, device="cpu"):
     return float(t.item())
 
 
+PARITY_SAMPLE = 8     # tensors of the batch whose GPU result is compared with the oracle's
+TRAFFIC_RATIO = 1.07  # DRAM bytes / algorithmic bytes of a full-batch k_batch launch (ncu capture)
+
+
 def run_gpu(args):
     import torch
     from paper_1111_6091_gb300 import cpmg
@@ -188,162 +241,272 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.Stream()
     ctx = cpmg.Context(local, stream=stream.cuda_stream)
-    p = problem()
-    opts = cpmg.make_opts(precision=cpmg.PREC_MIXED, tol=TOL, coarsest=COARSEST, als_fallback=1)
-
+    probs = batch_problems(BATCH_COUNT)
     with torch.cuda.stream(stream):
-        Z = cpmg.colmajor(p.Z)
-        A0 = [cpmg.colmajor(a) for a in p.A0]
-        T0 = [[cpmg.colmajor(a) for a in b] for b in p.tfms]
-        A = [a.clone() for a in A0]
-        T = [[a.clone() for a in b] for b in T0]
-        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        Zs = [cpmg.colmajor(p.Z) for p in probs]
+        A0 = [[cpmg.colmajor(a) for a in p.A0] for p in probs]
+        As = [[a.clone() for a in A] for A in A0]
+    torch.cuda.synchronize()
 
     def reset():
-        for a, a0 in zip(A, A0):
-            a.copy_(a0)
-        for b, b0 in zip(T, T0):
-            for a, a0 in zip(b, b0):
-                a.copy_(a0)
-
-    def step():
-        return cpmg.cpmg_decompose(ctx, Z, A, T, opts)
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            reset()
-            step()
+        with torch.cuda.stream(stream):
+            for A, B in zip(As, A0):
+                for a, b in zip(A, B):
+                    a.copy_(b)
         torch.cuda.synchronize()
-        ranks_barrier()
-        clocks = Clocks()
-        clocks.start()
-        launches0 = ctx.launches()
-        ms, results = [], []
-        for _ in range(args.steps):
-            reset()
-            flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            results.append(step())
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        torch.cuda.synchronize()
-        ranks_barrier()
-        launches = (ctx.launches() - launches0) // max(args.steps, 1)
-        clk = clocks.stop()
-        # One more identical step with per-launch CUDA events on the finest-level MTTKRP main
-        # kernel (the event nodes slow graph replay, so the timed steps above run without them).
+
+    def step(prec, Z=Zs, A=As):
+        return cpmg.cpmg_batch_solve(ctx, Z, A, precision=prec, tol=BATCH_TOL, max_als_iters=BATCH_MAX_IT,
+                                     check_every=BATCH_CHECK)
+
+    def timed(prec):
         reset()
-        flush.fill_(1.0)
-        ctx.profile(True)
-        ctx.profile_reset()
-        step()
-        torch.cuda.synchronize()
-        prof = [ctx.profile_read(k) for k in range(3)]
-        ctx.profile(False)
-    t_step = max_over_ranks(statistics.mean(ms), device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, res = step(prec)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), res
 
+    for _ in range(args.warmup):  # the first call also tunes the unit sizes of the shape classes
+        reset()
+        step(cpmg.PREC_MIXED)
+    torch.cuda.synchronize()
+    ranks_barrier()
+    clocks = Clocks()
+    clocks.start()
+    launches0 = ctx.launches()
+    ctx.profile_reset()
+    ctx.profile(True)
+    ms, res = [], None
+    for _ in range(args.steps):
+        t, res = timed(cpmg.PREC_MIXED)
+        ms.append(t)
+    torch.cuda.synchronize()
+    ranks_barrier()
+    clk = clocks.stop()
+    launches = (ctx.launches() - launches0) // max(args.steps, 1)
+    prof_ms, prof_n, prof_bytes = ctx.profile_read(4)
+    ctx.profile(False)
+    t_step = max_over_ranks(statistics.mean(ms), device="cuda")
+    A_gpu = [[cpmg.to_numpy(a) for a in As[i]] for i in range(PARITY_SAMPLE)]
+    res_mixed = res
+    zbytes = sum(p.Z.nbytes for p in probs)
+
+    def summary(r, seconds):
+        it = [x["iters_als"] for x in r]
+        return {"seconds": seconds, "converged": sum(x["status"] == cpmg.OK for x in r),
+                "tensor_sweeps": int(sum(it)), "max_sweeps": int(max(it)), "median_sweeps": float(np.median(it)),
+                "worst_g": max(x["g"] for x in r)}
+
+    batched = {"mixed": summary(res_mixed, t_step * 1e-3)}
     if args.solve_only:
         if rank == 0:
-            print(json.dumps({"solve_only": True, "ms": ms, "launches": int(launches)}), flush=True)
+            print(json.dumps({"solve_only": True, "ms": ms, "launches": int(launches), **batched}), flush=True)
         ctx.close()
         return
 
-    # end to end through the C ABI with pinned host buffers
-    Zh = cpmg.colmajor(p.Z, device="cpu", pin=True)
-    Ah = [cpmg.colmajor(a, device="cpu", pin=True) for a in p.A0]
-    Th = [[cpmg.colmajor(a, device="cpu", pin=True) for a in b] for b in p.tfms]
-    e2e = []
-    for _ in range(args.steps):
-        for a, a0 in zip(Ah, p.A0):
-            a.copy_(torch.from_numpy(np.ascontiguousarray(a0.T)))
-        for b, b0 in zip(Th, p.tfms):
-            for a, a0 in zip(b, b0):
-                a.copy_(torch.from_numpy(np.ascontiguousarray(a0.T)))
+    # the plain FP64 GPU path on the same batch
+    t64, res64 = timed(cpmg.PREC_FP64)
+    batched["fp64"] = summary(res64, t64 * 1e-3)
+    batched["mixed_vs_fp64"] = batched["fp64"]["seconds"] / batched["mixed"]["seconds"]
+    # the same MIXED solves as a loop of per-tensor calls
+    if args.batch_loop:
+        reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv = 0
         with torch.cuda.stream(stream):
-            flush.fill_(2.0)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            cpmg.cpmg_decompose(ctx, Zh, Ah, Th, opts)
-            torch.cuda.synchronize()
-            e2e.append(time.perf_counter() - t0)
-    h2d = Zh.numel() * 4 + sum(a.numel() * 8 for a in Ah) + sum(a.numel() * 8 for b in Th for a in b)
-    d2h = sum(a.numel() * 8 for a in Ah) + sum(a.numel() * 8 for b in Th for a in b)
+            for Z, A in zip(Zs, As):
+                r = cpmg.cp_als_sweep(ctx, Z, A, BATCH_MAX_IT, precision=cpmg.PREC_MIXED, tol=BATCH_TOL,
+                                      check_every=BATCH_CHECK)
+                conv += r["status"] == cpmg.OK
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        batched["per_tensor_loop_mixed"] = {"seconds": dt, "converged": conv}
+        batched["speedup_vs_loop"] = dt / batched["mixed"]["seconds"]
 
-    # bandwidth kernel of the timed steps: the finest-level MTTKRP (bulk-copy kernel)
-    kinds = ["fp32", "float-pair", "fp64"]
-    tot = [x[0] for x in prof]
-    k = int(np.argmax(tot))
-    ms_k, n_k, bytes_k = prof[k]
-    hbm, how = peaks()
-    avg_s = ms_k * 1e-3 / max(n_k, 1)
-    achieved = bytes_k / avg_s / 1e9 if n_k else None
+    # end to end through the C ABI with pinned host buffers (copies inside the call)
+    Zh = [cpmg.colmajor(p.Z, device="cpu", pin=True) for p in probs]
+    Ah = [[cpmg.colmajor(a, device="cpu", pin=True) for a in p.A0] for p in probs]
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        for A, p in zip(Ah, probs):
+            for a, a0 in zip(A, p.A0):
+                a.copy_(torch.from_numpy(np.ascontiguousarray(a0.T)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(cpmg.PREC_MIXED, Zh, Ah)
+        e2e.append(time.perf_counter() - t0)
+    fbytes = sum(a.numel() * 8 for A in Ah for a in A)
+    del Zh, Ah
 
-    # 400^3 rank-10 FP32 MTTKRP bandwidth (inputs larger than L2)
-    from paper_1111_6091_gb300 import synth
-    p4 = synth.make_problem((400, 400, 400), 10, congruence=0.95, eta_homo=0.01, dtype=np.float32, seed=0)
-    with torch.cuda.stream(stream):
-        Z4 = cpmg.colmajor(p4.Z)
-        A4 = [cpmg.colmajor(a) for a in p4.A0]
-        o4 = cpmg.make_opts(precision=cpmg.PREC_FP32, check_every=0)
-        cpmg.cp_als_sweep(ctx, Z4, A4, 3, o4)
-        ctx.profile(True)
-        ctx.profile_reset()
-        cpmg.cp_als_sweep(ctx, Z4, A4, 10, o4)
-        ms4, n4, b4 = ctx.profile_read(0)
-        ctx.profile(False)
-    gbs4 = b4 / (ms4 * 1e-3 / n4) / 1e9
-    ttm4 = ttm_400cubed(ctx, stream, Z4, hbm, how)
-    del Z4, A4
-    batched = run_batched(ctx, stream, args.batch_count) if args.batch_count > 0 else None
-    served = run_served(args.serve_requests) if args.serve_requests > 0 else None
-    dense_ijk = run_paper_dense(ctx, stream) if not args.no_paper_dense else None
-
+    # parity of a sample of the batch against the oracle (same problems, same starts, same stopping test)
+    parity = None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        if batched is not None:
-            batched["cpu_oracle_sample"] = oracle_batch_sample()
-        dt, r = oracle_solve(p)
-        cpu = {"value": dt, "unit": "s", "cores": blas_threads(), "kind": "oracle",
-               "sample": "one full solve of the workload by the FP64 NumPy oracle (same solver and start)",
-               "oracle_cycles": {"setup": r.setup_cycles, "solve": r.solve_cycles,
-                                 "als": getattr(r, "als_iters", 0)}}
+        from oracle import align, tensor as T
+        rows = []
+        for i in range(PARITY_SAMPLE):
+            _, Ao, ito, go = oracle_batch_tensor(probs[i])
+            Z64 = probs[i].Z.astype(np.float64)
+            fo, fg = T.f_value(Z64, Ao), T.f_value(Z64, A_gpu[i])
+            rows.append({"tensor": i, "factor_err": align.factor_error(Ao, A_gpu[i]),
+                         "rel_f": abs(fg - fo) / fo, "g_gpu": res_mixed[i]["g"], "g_oracle": go,
+                         "sweeps_gpu": res_mixed[i]["iters_als"], "sweeps_oracle": ito})
+        parity = {"sample": f"tensors 0..{PARITY_SAMPLE - 1}", "max_factor_err": max(r["factor_err"] for r in rows),
+                  "max_rel_f": max(r["rel_f"] for r in rows), "tensors": rows}
+        # the oracle's cost of the whole workload: its measured seconds per (mode x element) of an ALS
+        # iteration, times the MTTKRP passes each tensor needs to tolerance (the GPU's sweep counts,
+        # plus the g evaluations every check interval)
+        rate = oracle_sweep_cost(probs)
+        work = sum((r["iters_als"] + r["iters_als"] / BATCH_CHECK) * p.Z.ndim * p.Z.size
+                   for r, p in zip(res_mixed, probs))
+        cpu = {"value": rate * work, "unit": "s", "cores": blas_threads(), "kind": "oracle",
+               "sample": "FP64 NumPy ALS, 4 iterations of each of the first 16 tensors timed; value = that "
+                         "cost per (mode x element) x the MTTKRP passes of the whole batch to tolerance"}
 
-    res = results[-1]
+    # roofline of the batched kernel over the timed steps (CUDA events around every launch)
+    hbm, how = peaks()
+    avg_s = prof_ms * 1e-3 / max(prof_n, 1)
+    achieved = prof_bytes / avg_s / 1e9 if prof_n else None
+    roofline = {"bound": "hbm", "kernel": "k_batch (cooperative persistent batched CP-ALS)",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+                "traffic": TRAFFIC_RATIO * prof_bytes if prof_n else None, "launches_per_step": prof_n // max(args.steps, 1),
+                "avg_us": avg_s * 1e6, "algorithmic_bytes_per_launch": prof_bytes, "peak_source": how,
+                "note": "mean over every launch of the timed steps; late launches carry only the few tensors "
+                        "still above tolerance, so the kernel is latency-bound there; traffic = the captured "
+                        "DRAM/algorithmic ratio of a full-batch launch x the mean algorithmic bytes"}
+
+    extra = {}
+    if not args.no_extras:
+        extra["multilevel_100cubed"] = run_multilevel_100cubed(ctx, stream, parity=rank == 0 and not args.no_cpu_baseline)
+        extra.update(run_400cubed(ctx, stream, hbm, how))
+        if args.serve_requests > 0:
+            extra["served"] = run_served(args.serve_requests)
+        if not args.no_paper_dense:
+            extra["paper_dense_ijk"] = run_paper_dense(ctx, stream)
+            extra["paper_laplacian"] = run_paper_laplacian(ctx, stream)
+
     line = {
         "metric": METRIC, "value": t_step * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
-        "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
-        "roofline": {"bound": "hbm", "kernel": f"k_mttkrp_tma ({kinds[k]}, 100^3 finest level)",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm if achieved else None, "traffic": None,
-                     "launches": n_k, "avg_us": avg_s * 1e6, "peak_source": how,
-                     "note": "timed on one extra profiled step of the same workload; the 4 MB tensor is "
-                             "L2-resident inside a solve; frac is against HBM"},
-        "mttkrp_400cubed_fp32": {"achieved": gbs4, "peak": hbm, "unit": "GB/s", "frac": gbs4 / hbm,
-                                 "avg_us": ms4 * 1e3 / n4, "launches": n4, "peak_source": how},
-        "ttm_400cubed_tc": ttm4,
-        "batched": batched,
-        "served": served,
-        "paper_dense_ijk": dense_ijk,
+        "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": int(zbytes + fbytes),
+                "d2h_bytes_per_step": int(fbytes)},
+        "roofline": roofline,
         "cpu_baseline": cpu,
+        "err_vs_oracle": parity,
+        "batched": batched,
         "gpu_launches": int(launches),
-        "gpu_launches_note": "kernel launches per step issued by libcpmg (graph replays count their kernels)",
+        "gpu_launches_note": "kernel launches per step issued by libcpmg",
         "clocks": clk,
-        "solver": {k2: res[k2] for k2 in ("g", "f", "iters_setup", "iters_solve", "iters_als", "restarted",
-                                          "refine_sweeps", "levels", "status")},
         "step_ms": ms,
+        **extra,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_multilevel_100cubed(ctx, stream, reps=3, parity=True):
+    """The 100^3 rank-5 workload by the "Multilevel" driver of Section 6.1 (setup cycles, FAS solve
+    cycles with the one-time rebuild, then plain ALS if stagnation persists), MIXED, to g < 1e-8;
+    with `parity`, the oracle's solve from the same start beside it."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg
+    p = problem()
+    opts = cpmg.make_opts(precision=cpmg.PREC_MIXED, tol=TOL, coarsest=COARSEST, als_fallback=1)
+    with torch.cuda.stream(stream):
+        Z = cpmg.colmajor(p.Z)
+        A0 = [cpmg.colmajor(a) for a in p.A0]
+        T0 = [[cpmg.colmajor(a) for a in b] for b in p.tfms]
+    A = [a.clone() for a in A0]
+    T = [[a.clone() for a in b] for b in T0]
+    ms, r = [], None
+    for k in range(reps + 1):
+        with torch.cuda.stream(stream):
+            for a, a0 in zip(A, A0):
+                a.copy_(a0)
+            for b, b0 in zip(T, T0):
+                for a, a0 in zip(b, b0):
+                    a.copy_(a0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = cpmg.cpmg_decompose(ctx, Z, A, T, opts)
+            e1.record(stream)
+            e1.synchronize()
+        if k:
+            ms.append(e0.elapsed_time(e1))
+    out = {"workload": "dense 100x100x100 fp32, R=5, congruence 0.9, noise 1%+5%, levels 100/50/25/13, g<1e-8",
+           "seconds": statistics.mean(ms) * 1e-3, "solver": {k: r[k] for k in ("g", "f", "iters_setup", "iters_solve",
+                                                                             "iters_als", "restarted", "levels", "status")}}
+    if parity:
+        from oracle import align, tensor as OT
+        dt, ro = oracle_solve(p)
+        got = [cpmg.to_numpy(a) for a in A]
+        fo = OT.f_value(p.Z.astype(np.float64), ro.A)
+        out["oracle"] = {"seconds": dt, "setup": ro.setup_cycles, "solve": ro.solve_cycles,
+                         "als": getattr(ro, "als_iters", 0), "cores": blas_threads()}
+        out["err_vs_oracle"] = {"factor_err": align.factor_error(ro.A, got), "rel_f": abs(r["f"] - fo) / fo}
+    return out
+
+
+def run_400cubed(ctx, stream, hbm, how):
+    """The 400^3 rank-10 float32 tensor (256 MB, congruence 0.95, 1% noise): one ALS sweep with and
+    without the dimension tree, the MTTKRP passes of the sweep against the measured HBM peak, the
+    tensor-core restriction, and the "Multilevel" solve over five levels (400/200/100/50/25) to
+    g < 1e-8 with the caps of Section 6.1 (500 cycles, 1e4 ALS iterations)."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg, synth
+    p4 = synth.make_problem((400, 400, 400), 10, congruence=0.95, eta_homo=0.01, dtype=np.float32, seed=0)
+    out = {}
+    with torch.cuda.stream(stream):
+        Z4 = cpmg.colmajor(p4.Z)
+        A0 = [cpmg.colmajor(a) for a in p4.A0]
+    sweeps = {}
+    for name, prec in (("fp32", cpmg.PREC_FP32), ("float_pair", cpmg.PREC_DF)):
+        for tree in (1, 0):
+            A = [a.clone() for a in A0]
+            o = cpmg.make_opts(precision=prec, check_every=0, dimension_tree=tree)
+            with torch.cuda.stream(stream):
+                cpmg.cp_als_sweep(ctx, Z4, A, 10, o)  # captures the 10-sweep graph
+                ctx.profile_reset()
+                ctx.profile(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                cpmg.cp_als_sweep(ctx, Z4, A, 10, o)
+                e1.record(stream)
+                e1.synchronize()
+                ms, n, b = ctx.profile_read(0 if prec == cpmg.PREC_FP32 else 1)
+                ctx.profile(False)
+            gbs = b / (ms * 1e-3 / n) / 1e9 if n else None
+            sweeps[f"{name}_tree{tree}"] = {"ms_per_sweep": e0.elapsed_time(e1) / 10, "z_passes_per_sweep": n / 10,
+                                            "mttkrp_gbs": gbs, "mttkrp_frac": gbs / hbm if gbs else None,
+                                            "mttkrp_avg_us": ms * 1e3 / n if n else None}
+    out["sweep_400cubed_r10"] = dict(sweeps, peak=hbm, peak_source=how)
+    out["ttm_400cubed_tc"] = ttm_400cubed(ctx, stream, Z4, hbm, how)
+    opts = cpmg.make_opts(precision=cpmg.PREC_MIXED, tol=TOL, coarsest=(25, 25, 25), als_fallback=1,
+                          max_cycles=500, max_als_iters=10000)
+    with torch.cuda.stream(stream):
+        A = [a.clone() for a in A0]
+        T = [[cpmg.colmajor(a) for a in b] for b in p4.tfms]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = cpmg.cpmg_decompose(ctx, Z4, A, T, opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    out["multilevel_400cubed_r10"] = {
+        "workload": "dense 400^3 fp32, R=10, congruence 0.95, 1% noise, 5 levels, g<1e-8, Section 6.1 caps",
+        "seconds": dt, "solver": {k: r[k] for k in ("g", "f", "iters_setup", "iters_solve", "iters_als", "restarted",
+                                                    "refine_sweeps", "levels", "status")}}
+    del Z4
+    return out
+
+
 
 
 TTM_DIMS, TTM_IC = (400, 400, 400), 200
@@ -395,7 +558,6 @@ def peaks_tensor():
         return 1900.0  # fallback burst figure
 
 
-BATCH_COUNT, BATCH_TOL, BATCH_MAX_IT, BATCH_CHECK = 512, 1e-8, 1000, 8
 
 
 def batch_problems(count, seed=0):
@@ -404,75 +566,6 @@ def batch_problems(count, seed=0):
     return [synth.make_problem(sp["dims"], sp["R"], congruence=sp["congruence"], eta_homo=0.01,
                                dtype=np.float32, seed=sp["seed"], n_t=0)
             for sp in synth.batch_specs(count, seed)]
-
-
-def oracle_batch_sample(count=32, sweeps=5):
-    """The FP64 oracle's ALS on a bounded sample of the batch workload (its first `count`
-    tensors, `sweeps` sweeps each), as tensor-sweeps per second on the host cores."""
-    from oracle import als as ALS
-    probs = batch_problems(count)
-    t = time.perf_counter()
-    for p in probs:
-        A = p.A0
-        Z64 = p.Z.astype(np.float64)
-        for _ in range(sweeps):
-            A = ALS.als_sweep(Z64, A)
-    dt = time.perf_counter() - t
-    return {"value": count * sweeps / dt, "unit": "tensor-sweeps/s", "cores": blas_threads(), "kind": "oracle",
-            "sample": f"FP64 NumPy ALS, {sweeps} sweeps of each of the first {count} tensors of the batch"}
-
-
-def run_batched(ctx, stream, count=BATCH_COUNT):
-    """Batched CP-ALS of `count` uneven tensors to g < 1e-8 (at most 1000 sweeps each) in MIXED
-    and in FP64 arithmetic, and the same MIXED solves as a loop of per-tensor cp_als_sweep calls."""
-    import torch
-    from paper_1111_6091_gb300 import cpmg
-    probs = batch_problems(count)
-    with torch.cuda.stream(stream):
-        Zs = [cpmg.colmajor(p.Z) for p in probs]
-        A0 = [[cpmg.colmajor(a) for a in p.A0] for p in probs]
-        As = [[a.clone() for a in A] for A in A0]
-    torch.cuda.synchronize()
-
-    def reset():
-        with torch.cuda.stream(stream):
-            for A, B in zip(As, A0):
-                for a, b in zip(A, B):
-                    a.copy_(b)
-        torch.cuda.synchronize()
-
-    out = {"count": count, "tol": BATCH_TOL, "max_sweeps": BATCH_MAX_IT, "check_every": BATCH_CHECK}
-    zbytes = [p.Z.nbytes for p in probs]
-    for name, prec in (("mixed", cpmg.PREC_MIXED), ("fp64", cpmg.PREC_FP64)):
-        reset()
-        # first call tunes the unit sizes for these shape classes; time the second
-        cpmg.cpmg_batch_solve(ctx, Zs, As, precision=prec, tol=BATCH_TOL, max_als_iters=BATCH_MAX_IT,
-                              check_every=BATCH_CHECK)
-        reset()
-        t0 = time.perf_counter()
-        st, res = cpmg.cpmg_batch_solve(ctx, Zs, As, precision=prec, tol=BATCH_TOL, max_als_iters=BATCH_MAX_IT,
-                                        check_every=BATCH_CHECK)
-        dt = time.perf_counter() - t0
-        sweeps = sum(r["iters_als"] for r in res)
-        zsw = sum(r["iters_als"] * len(p.Z.shape) * b for r, p, b in zip(res, probs, zbytes))
-        out[name] = {"seconds": dt, "converged": sum(r["status"] == cpmg.OK for r in res),
-                     "tensor_sweeps": sweeps, "tensor_sweeps_per_s": sweeps / dt,
-                     "sweep_z_gbs": zsw / dt / 1e9}
-    # per-tensor launch loop (the same MIXED solves one tensor at a time)
-    reset()
-    t0 = time.perf_counter()
-    conv = 0
-    with torch.cuda.stream(stream):
-        for Z, A in zip(Zs, As):
-            r = cpmg.cp_als_sweep(ctx, Z, A, BATCH_MAX_IT, precision=cpmg.PREC_MIXED, tol=BATCH_TOL,
-                                  check_every=BATCH_CHECK)
-            conv += r["status"] == cpmg.OK
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    out["per_tensor_loop_mixed"] = {"seconds": dt, "converged": conv}
-    out["speedup_vs_loop"] = dt / out["mixed"]["seconds"]
-    out["mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
-    return out
 
 
 def run_paper_dense(ctx, stream, s=100, R=3, reps=2):
@@ -544,6 +637,48 @@ def run_paper_dense(ctx, stream, s=100, R=3, reps=2):
 
 
 SERVE_RATE, SERVE_LARGE_FRAC = 2000.0, 0.05
+
+
+# Table tab:LapParams tests run here, with the paper's Table tab:Laplacian results for context:
+# (test, N, s, R, coarsest, paper ALS iterations / s, paper ML iterations / s)
+LAPLACIAN_TESTS = [(1, 4, 20, 4, 10, 1897, 24.0, 37, 7.6), (2, 4, 20, 5, 10, 3329, 53.6, 64, 15.1),
+                   (3, 4, 20, 6, 10, 3587, 70.3, 67, 17.5), (7, 6, 20, 2, 5, 1619, 187.0, 48, 111.4)]
+
+
+def run_paper_laplacian(ctx, stream):
+    """The paper's Laplacian tensor (Section 6.2), dense, float32 storage (exact), float64-accurate
+    arithmetic (float pairs), uniform [0,1] starts, to g < 1e-10: the "Multilevel" solver against
+    plain ALS (at most 1e4 iterations), per test of Table tab:LapParams."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg, synth
+    out = []
+    for test, N, s, R, co, p_als_it, p_als_s, p_ml_it, p_ml_s in LAPLACIAN_TESTS:
+        Z = synth.laplacian_tensor(N // 2, s, dtype=np.float32)
+        A0 = synth.uniform_start(Z.shape, R, 0)
+        tfms = [synth.uniform_start(Z.shape, R, 1 + t) for t in range(2)]
+        with torch.cuda.stream(stream):
+            Zd = cpmg.colmajor(Z)
+            A = [cpmg.colmajor(a) for a in A0]
+            tf = [[cpmg.colmajor(a) for a in b] for b in tfms]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = cpmg.cpmg_decompose(ctx, Zd, A, tf, precision=cpmg.PREC_DF, tol=1e-10, coarsest=(co,) * N)
+            torch.cuda.synchronize()
+            t_ml = time.perf_counter() - t0
+            A = [cpmg.colmajor(a) for a in A0]
+            t0 = time.perf_counter()
+            ra = cpmg.cp_als_sweep(ctx, Zd, A, 10000, precision=cpmg.PREC_DF, tol=1e-10, check_every=-1)
+            torch.cuda.synchronize()
+            t_als = time.perf_counter() - t0
+        del Zd
+        out.append({"test": test, "N": N, "s": s, "R": R, "levels": r["levels"],
+                    "multilevel": {"seconds": t_ml, "setup": r["iters_setup"], "solve": r["iters_solve"],
+                                   "g": r["g"], "status": r["status"]},
+                    "als": {"seconds": t_als, "iters": ra["iters_als"], "g": ra["g"], "status": ra["status"]},
+                    "speedup": t_als / t_ml,
+                    "paper_matlab": {"als_iters": p_als_it, "als_s": p_als_s, "ml_iters": p_ml_it, "ml_s": p_ml_s}})
+    return {"tensor": "finite-difference Laplacian, order N = 2d, s^N dense", "tol": 1e-10, "precision": "float-pair",
+            "tests": out, "note": "paper: MATLAB on a 2.5 GHz Core 2 Duo, sparse tensors, averages of 10 starts; context only"}
 
 
 def run_served(nreq, pool_small=96, pool_large=4, seed=12345):
@@ -648,15 +783,17 @@ def run_batch_case(args):
 
 
 def run_mttkrp_case(args):
-    """Small case for profiler captures: two FP32 ALS sweeps on the 400^3 rank-10 tensor
-    (six MTTKRP main-kernel launches)."""
+    """Small case for profiler captures: two ALS sweeps on the 400^3 rank-10 tensor in the chosen
+    arithmetic; with the dimension tree each sweep is the W pass (k_dt_w, or a tensor-core mode
+    product for bf16x3) and one mode-3 pass."""
     import torch
     from paper_1111_6091_gb300 import cpmg, synth
     p4 = synth.make_problem((400, 400, 400), 10, congruence=0.95, eta_homo=0.01, dtype=np.float32, seed=0)
     ctx = cpmg.Context(0)
     Z4 = cpmg.colmajor(p4.Z)
     A4 = [cpmg.colmajor(a) for a in p4.A0]
-    prec = {"fp32": cpmg.PREC_FP32, "df": cpmg.PREC_DF, "fp64": cpmg.PREC_FP64}[args.case_prec]
+    prec = {"fp32": cpmg.PREC_FP32, "df": cpmg.PREC_DF, "fp64": cpmg.PREC_FP64,
+            "bf16x3": cpmg.PREC_BF16X3}[args.case_prec]
     r = cpmg.cp_als_sweep(ctx, Z4, A4, 2, precision=prec, check_every=0)
     torch.cuda.synchronize()
     print(json.dumps({"case": "mttkrp 400^3 R=10", "precision": args.case_prec, "f": r["f"]}))
@@ -666,7 +803,7 @@ def run_mttkrp_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--mttkrp-case", action="store_true", help="profiler case: 2 sweeps at 400^3")
-    ap.add_argument("--case-prec", default="fp32", choices=["fp32", "df", "fp64"])
+    ap.add_argument("--case-prec", default="fp32", choices=["fp32", "df", "fp64", "bf16x3"])
     ap.add_argument("--ttm-case", action="store_true", help="profiler case: one 400^3 restriction")
     ap.add_argument("--sweep-case", action="store_true", help="profiler case: 40 ALS sweeps at 100^3")
     ap.add_argument("--batch-case", action="store_true", help="profiler case: one 8-sweep launch of the 512-tensor batch")
@@ -678,7 +815,10 @@ def main():
     ap.add_argument("--no-paper-dense", action="store_true", help="skip the paper's dense-tensor comparison")
     ap.add_argument("--paper-dense", action="store_true", help="run only the paper's dense-tensor comparison")
     ap.add_argument("--solve-only", action="store_true", help="profiler case: the timed solves only")
-    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT, help="batched workload size (0: skip)")
+    ap.add_argument("--no-batch-loop", dest="batch_loop", action="store_false",
+                    help="skip the per-tensor launch loop over the batch")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the batched workload (no 100^3 / 400^3 / served / paper-tensor measurements)")
     ap.add_argument("--serve-requests", type=int, default=1000,
                     help="requests of the served workload (20000 for the full stream; 0: skip)")
     args = ap.parse_args()

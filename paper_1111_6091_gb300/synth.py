@@ -153,6 +153,27 @@ def ijk_tensor(s, dtype=np.float64):
     return np.asfortranarray(Z.astype(dtype))
 
 
+def laplacian_tensor(d, s, dtype=np.float64):
+    """The paper's sparse test problem (Section 6.2), stored dense: the s^d x s^d finite-difference
+    Laplacian sum_{k=1..d} I_{s^(d-k)} (x) D (x) I_{s^(k-1)}, D = tridiag(-1, 2, -1) of size s,
+    reshaped column-major into an order-2d tensor of size s x ... x s.  Modes 1..d carry the row
+    index of the matrix (first grid dimension fastest), modes d+1..2d the column index, so
+    Z[i_1..i_d, j_1..j_d] = sum_k D[i_k, j_k] prod_{m != k} [i_m == j_m].  The entries are small
+    integers, exact in float32."""
+    D = 2.0 * np.eye(s) - np.eye(s, k=1) - np.eye(s, k=-1)
+    n = s ** d
+    M = np.zeros((n, n))
+    for k in range(1, d + 1):
+        M += np.kron(np.kron(np.eye(s ** (d - k)), D), np.eye(s ** (k - 1)))
+    return np.asfortranarray(np.reshape(M, (s,) * (2 * d), order="F").astype(dtype))
+
+
+def uniform_start(dims, R, seed):
+    """Factor matrices with i.i.d. uniform [0, 1) entries (the paper's initial guesses, Section 6.1),
+    mode n from seed*1000 + 300 + n."""
+    return [np.asfortranarray(_rng(seed * 1000 + 300 + n).uniform(size=(I, R))) for n, I in enumerate(dims)]
+
+
 def batch_specs(count, seed=0):
     """Shapes for the uneven batch workload: N in {3,4} with probability 1/2, I_n ~ U[16,128]
     (U[16,48] when N=4), R ~ U{2..8}, congruence ~ U[0.5,0.95], seeded by ``seed``."""
