@@ -933,10 +933,31 @@ struct BItem {                   // one problem as given by the caller
   cpmg_opts o;
   int64_t target;                // elements per MTTKRP unit (autotuned per shape class)
   bool has_state;
+  bool late;                     // past kLateSweeps: kLateUnit-element units, not the tuned size
   BTen state;                    // device state carried over when the batch is rebuilt
 };
 
 static int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// A tensor still running after kLateSweeps sweeps switches to the smallest unit size: the tuned
+// sizes favour throughput over a full batch, while the few tensors left late in a solve are
+// latency-bound (a lone 40x126x48 rank-8 float-pair sweep: 0.41 ms at 32k-element units, 0.16 ms
+// at 2k).  The switch depends only on the tensor's own sweep count, so its arithmetic is the same
+// alone, in any batch, and in the server.
+constexpr int kLateSweeps = 512;
+constexpr int64_t kLateUnit = 2048;
+
+// Marks the loaded tensors that crossed kLateSweeps; true when any unit list must be rebuilt.
+static bool late_switch(std::vector<BItem*>& items, const std::vector<BTen>& host) {
+  bool changed = false;
+  for (size_t j = 0; j < items.size(); ++j)
+    if (!items[j]->late && host[j].active && host[j].iters >= kLateSweeps) {
+      items[j]->late = true;
+      items[j]->target = std::min<int64_t>(items[j]->target, kLateUnit);
+      changed = true;
+    }
+  return changed;
+}
 
 static int64_t numel_of(const BItem& it) {
   int64_t P = 1;
@@ -1308,6 +1329,7 @@ static int autotune(BatchDev& B, std::vector<BItem>& items) {
   BatchState* S = state_of(B.c);
   std::vector<int> todo;
   for (size_t t = 0; t < items.size(); ++t) {
+    if (items[t].late) continue;  // keeps its late unit size
     if (S->fixed_target > 0) {
       items[t].target = S->fixed_target;
       continue;
@@ -1448,10 +1470,13 @@ static void server_loop(cpmg_ctx* c, BatchState* S) {
     std::vector<int> fin;
     {
       std::lock_guard<std::mutex> lk(S->mu);  // cancel flags are set by other threads
+      std::vector<BItem*> cur;
       for (size_t t = 0; t < S->active.size(); ++t) {
         S->active[t]->item.state = B.host[t];
+        cur.push_back(&S->active[t]->item);
         if (!B.host[t].active || S->active[t]->cancel) fin.push_back((int)t);
       }
+      if (late_switch(cur, B.host)) dirty = true;
     }
     if (!fin.empty()) {
       if ((rc = batch_sort(B, fin)) != CPMG_OK) break;
@@ -1636,9 +1661,14 @@ static int batch_solve_dev(cpmg_ctx* c, int count, const cpmg_tensor* Z, const i
     int nact = count;
     for (int64_t l = 0; l < maxl && nact > 0 && st == CPMG_OK; ++l) {
       st = batch_step(B, k, &nact, true);
-      if (st != CPMG_OK || nact == 0 || nact * 2 > (int)loaded.size()) continue;
-      // at most half the loaded tensors still run: reload only those (their state carries over;
-      // each tensor's units, partial slots and sums are its own, so its arithmetic is unchanged)
+      if (st != CPMG_OK || nact == 0) continue;
+      std::vector<BItem*> cur(loaded.size());
+      for (size_t j = 0; j < loaded.size(); ++j) cur[j] = &items[loaded[j]];
+      const bool late = late_switch(cur, B.host);
+      if (!late && nact * 2 > (int)loaded.size()) continue;
+      // reload only the tensors still running (at most half of those loaded, or some switched to
+      // late units); their state carries over, and each tensor's units, partial slots and sums
+      // are its own, so its arithmetic does not depend on the others
       std::vector<BItem> act;
       std::vector<int> idx;
       for (size_t j = 0; j < loaded.size(); ++j) {
