@@ -320,6 +320,18 @@ int cpmg_server_config(cpmg_ctx* ctx, size_t hbm_budget_bytes, int max_active, i
 /* Queue a request; *ticket identifies it.  CPMG_OUT_OF_BUDGET if it alone exceeds the budget. */
 int cpmg_server_submit(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A, const cpmg_opts* opts,
                        uint64_t* ticket);
+/* Queue a request for the "Multilevel" driver of Section 6.1 (the same solve as cpmg_decompose:
+ * setup cycles of Algorithm 1, then CP-FAS cycles of Algorithm 2) instead of batched ALS.  It runs
+ * on one of the server's multilevel workers, each with a context and stream of its own, so its
+ * launches overlap the batched requests'; its hierarchy (coarse tensors, operators, factor sets)
+ * is held on the device from its start to its end and counted against the server's HBM budget.
+ * Z: device tensor of order 2..CPMG_MAX_MODES; A: N device float64 I_n x R arrays (start in,
+ * result out); A_test: opts->n_t x N device arrays (the test factor matrices, as for
+ * cpmg_decompose), read only.  Z, A and A_test must stay valid until polled as done.  Its result
+ * does not depend on the other requests.  A running multilevel request is not cancelled (it is
+ * one solver call); a queued one is.  Same statuses as cpmg_server_submit. */
+int cpmg_server_submit_multilevel(cpmg_ctx* ctx, const cpmg_tensor* Z, int R, double* const* A,
+                                  double* const* A_test, const cpmg_opts* opts, uint64_t* ticket);
 /* CPMG_PENDING while queued or running; CPMG_OK once done, with *result (seconds = latency
  * from submission); the ticket is then released.  CPMG_INVALID_ARG for an unknown ticket. */
 int cpmg_server_poll(cpmg_ctx* ctx, uint64_t ticket, cpmg_result* result);

@@ -99,6 +99,8 @@ _SIGS = {
     "cpmg_server_config": (C.c_int, [_P, C.c_size_t, C.c_int, C.c_int, C.c_int64]),
     "cpmg_debug_config": (C.c_int, [_P, C.c_double, C.c_int]),
     "cpmg_server_cancel": (C.c_int, [_P, C.c_uint64]),
+    "cpmg_server_submit_multilevel": (C.c_int, [_P, C.POINTER(cpmg_tensor), C.c_int, _PP, _PP,
+                                                C.POINTER(cpmg_opts), C.POINTER(C.c_uint64)]),
     "cpmg_server_submit": (C.c_int, [_P, C.POINTER(cpmg_tensor), C.c_int, _PP, C.POINTER(cpmg_opts),
                                      C.POINTER(C.c_uint64)]),
     "cpmg_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(cpmg_result)]),
@@ -313,6 +315,21 @@ class Server:
         _check(lib().cpmg_server_submit(self.ctx.h, C.byref(d), A[0].shape[0], p, C.byref(o), C.byref(t)),
                "cpmg_server_submit")
         self._keep[t.value] = (Z, A, p)
+        return t.value
+
+    def submit_multilevel(self, Z, A, A_test, opts=None, **kw):
+        """Queue a request for the multilevel driver (Section 6.1); A_test: n_t blocks of N arrays."""
+        o = opts or make_opts(**kw)
+        o.n_t = len(A_test)
+        d = tensor_desc(Z)
+        p = _ptrs(A)
+        flat = [a for blk in A_test for a in blk]
+        pt = _ptrs(flat)
+        t = C.c_uint64()
+        _check(lib().cpmg_server_submit_multilevel(self.ctx.h, C.byref(d), A[0].shape[0], C.cast(p, _PP),
+                                                   C.cast(pt, _PP), C.byref(o), C.byref(t)),
+               "cpmg_server_submit_multilevel")
+        self._keep[t.value] = (Z, A, A_test, p, pt)
         return t.value
 
     def poll(self, ticket):

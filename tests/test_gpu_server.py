@@ -128,3 +128,47 @@ def test_budget_admission():
         assert r1["iters_als"] == r2["iters_als"]
         for a, b in zip(A1, A2):
             assert np.array_equal(a, b)
+
+
+def test_multilevel_requests_match_decompose_alone_and_in_the_mix(cpmg_ctx):
+    """A multilevel request (the Section 6.1 driver, hierarchy resident while it runs) gives the
+    factors of a direct cpmg_decompose call bitwise, whether it is served alone or beside batched
+    ALS requests and another multilevel request."""
+    import torch
+    from paper_1111_6091_gb300 import cpmg, synth
+    p = synth.make_problem((32, 30, 28), 3, congruence=0.5, eta_homo=0.001, dtype=np.float32, seed=4)
+    kw = dict(precision=cpmg.PREC_MIXED, tol=1e-9, coarsest=(8, 8, 8), als_fallback=1)
+    Z = cpmg.colmajor(p.Z)
+    A_ref = [cpmg.colmajor(a) for a in p.A0]
+    r_ref = cpmg.cpmg_decompose(cpmg_ctx, Z, A_ref, [[cpmg.colmajor(a) for a in b] for b in p.tfms], **kw)
+    assert r_ref["status"] == cpmg.OK
+    others = [synth.make_problem(d, 3, congruence=0.6, eta_homo=0.01, dtype=np.float32, seed=70 + k, n_t=2)
+              for k, d in enumerate([(24, 20, 18), (40, 36, 30), (30, 30, 30)])]
+    for mix in (False, True):
+        ctx = cpmg.Context(0)
+        try:
+            srv = cpmg.Server(ctx)
+            A = [cpmg.colmajor(a) for a in p.A0]
+            TF = [[cpmg.colmajor(a) for a in b] for b in p.tfms]
+            keep = []
+            if mix:
+                for q in others[:2]:
+                    Aq = [cpmg.colmajor(a) for a in q.A0]
+                    keep.append((srv.submit(cpmg.colmajor(q.Z), Aq, precision=cpmg.PREC_MIXED, tol=1e-8,
+                                            max_als_iters=2000), Aq))
+            t = srv.submit_multilevel(Z, A, TF, **kw)
+            if mix:
+                q = others[2]
+                Aq = [cpmg.colmajor(a) for a in q.A0]
+                keep.append((srv.submit_multilevel(cpmg.colmajor(q.Z), Aq, [[cpmg.colmajor(a) for a in b]
+                                                                              for b in q.tfms], **kw), Aq))
+            assert srv.wait(300.0) == cpmg.OK
+            r = srv.poll(t)
+            assert r["status"] == cpmg.OK and r["iters_setup"] == r_ref["iters_setup"]
+            for tk, _ in keep:
+                assert srv.poll(tk)["status"] in (cpmg.OK, cpmg.NOT_CONVERGED)
+            torch.cuda.synchronize()
+            for a, b in zip(A, A_ref):
+                assert np.array_equal(cpmg.to_numpy(a), cpmg.to_numpy(b)), mix
+        finally:
+            ctx.close()
