@@ -44,7 +44,9 @@ constexpr int kBThreads = 256;
 constexpr int kBWarps = kBThreads / 32;
 constexpr int kGramStride = kBR * kBR;
 
-enum { BP_FP32 = 0, BP_FP64 = 1, BP_DF = 3 };
+// BP_DELTA: float64-accurate sweeps computed as M = M_ref + Z_(n) (KR(A) - KR(A_ref)), with M_ref and
+// A_ref from the tensor's last g evaluation (float-pair products) and the correction in FP32
+enum { BP_FP32 = 0, BP_FP64 = 1, BP_DF = 3, BP_DELTA = 4 };
 enum { BS_RUNNING = -1 };
 
 // One problem of the batch (device copy; the kernel updates the state fields).
@@ -53,6 +55,9 @@ struct BTen {
   double* A[kBModes];
   float* Ah[kBModes];           // A as float pairs (hi, lo), same layout; kept when shadow != 0
   float* Al[kBModes];
+  float* Rh[kBModes];           // A_ref as float pairs: the factors at the last g evaluation
+  float* Rl[kBModes];
+  double* mref;                 // M_ref^(n) of every mode at A_ref, row r of mode n at kBR (off_n + i)
   double* gram;                 // kBModes x 8 x 8
   double* ginv;                 // 8 x 8: (Gamma^(n))^+ of the next mode to update
   float* gih;                   // ginv as float pairs (8 x 8 each)
@@ -71,6 +76,7 @@ struct BTen {
   int status;
   int iters, max_iters;
   int stall;
+  int no_delta;                 // 1: delta sweeps stopped helping (g stalled): float pairs to the end
   int check_k;                  // sweeps between this tensor's g evaluations (0: the launch's sweeps)
   int next_check;               // iteration count at which its next evaluation is due
   double g_prev;                // g at its previous evaluation
@@ -115,6 +121,7 @@ template <int P> struct BT;
 template <> struct BT<BP_FP32> { using V = float; };
 template <> struct BT<BP_FP64> { using V = double; };
 template <> struct BT<BP_DF> { using V = df; };
+template <> struct BT<BP_DELTA> { using V = float; };
 
 template <typename V> __device__ __forceinline__ V bzero();
 template <> __device__ __forceinline__ float bzero<float>() { return 0.f; }
@@ -406,6 +413,145 @@ __device__ void unit_run(const BTen& T, const BUnit& u, int lane, void* wsv, uin
   }
 }
 
+// MTTKRP unit of a delta sweep (BP_DELTA, float tensors): the Khatri-Rao rows of the current factors
+// and of A_ref are formed in float pairs and their difference is rounded to float; the products with
+// Z accumulate in FP32.  Their rounding scales with the factor change since A_ref, not with M.  For
+// mode n > 0 the unit also carries mode 1: A1 W - A1ref Wref = A1 (W - Wref) + (A1 - A1ref) Wref, so
+// each FP32 sum is multiplied by a small factor or is small itself.
+template <int RB>
+__device__ void unit_run_delta(const BTen& T, const BUnit& u, int lane, void* wsv, uint32_t* wc) {
+  float2* ws = reinterpret_cast<float2*>(wsv);  // (W - Wref, Wref) per column and rank
+  const int N = T.N, R = T.R, n = u.mode;
+  uint32_t dims[kBModes];
+#pragma unroll
+  for (int m = 0; m < kBModes; ++m) dims[m] = (uint32_t)T.dims[m];
+  const uint32_t I0 = dims[0];
+  const float* Z = reinterpret_cast<const float*>(T.Z);
+  uint32_t Lp = 1;
+#pragma unroll
+  for (int m = 1; m < kBModes; ++m)
+    if (m < n) Lp *= dims[m];
+  const uint32_t In = dims[n < kBModes ? n : 0];
+  const uint32_t r0 = (uint32_t)u.rb * kBRows;
+  const uint32_t rend = (r0 + kBRows < I0) ? r0 + kBRows : I0;
+  const uint32_t c1 = (uint32_t)u.c1, inx = (uint32_t)u.in_idx;
+  float acc1[2][RB], acc2[2][RB];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc1[q][r] = acc2[q][r] = 0.f;
+  const uint32_t i1a = r0 + lane, i1b = r0 + lane + 32;
+  const bool va = i1a < rend, vb = i1b < rend;
+  for (uint32_t jb = (uint32_t)u.c0; jb < c1; jb += 32) {
+    const int cnt = (int)(c1 - jb < 32 ? c1 - jb : 32);
+    if (lane < cnt) {
+      const uint32_t j = jb + lane;
+      const uint32_t col = (n == 0) ? j : (j % Lp) + Lp * (inx + In * (j / Lp));
+      wc[lane] = col;
+      df w[RB], wr[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) w[r] = wr[r] = df{1.f, 0.f};
+      uint32_t rem = col;
+#pragma unroll
+      for (int m = 1; m < kBModes; ++m) {
+        if (m < N) {
+          const uint32_t Im = dims[m];
+          const uint32_t im = rem % Im;
+          rem /= Im;
+          if (m != n) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+              if (r < R) {
+                const size_t e = im + (size_t)Im * r;
+                w[r] = df_mul(w[r], df{T.Ah[m][e], T.Al[m][e]});
+                wr[r] = df_mul(wr[r], df{T.Rh[m][e], T.Rl[m][e]});
+              }
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const df d = df_add(w[r], df{-wr[r].hi, -wr[r].lo});
+        ws[lane * RB + r] = r < R ? make_float2(__fadd_rn(d.hi, d.lo), __fadd_rn(wr[r].hi, wr[r].lo))
+                                  : make_float2(0.f, 0.f);
+      }
+    }
+    __syncwarp();
+    int jj = 0;
+    for (; jj + 8 <= cnt; jj += 8) {  // 16 loads in flight per lane, as the FP32 sweep
+      float za[8], zb[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const size_t base = (size_t)I0 * wc[jj + c];
+        za[c] = va ? Z[base + i1a] : 0.f;
+        zb[c] = vb ? Z[base + i1b] : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const float2 wv = ws[(jj + c) * RB + r];
+          acc1[0][r] = __fmaf_rn(za[c], wv.x, acc1[0][r]);
+          acc1[1][r] = __fmaf_rn(zb[c], wv.x, acc1[1][r]);
+          if (n != 0) {
+            acc2[0][r] = __fmaf_rn(za[c], wv.y, acc2[0][r]);
+            acc2[1][r] = __fmaf_rn(zb[c], wv.y, acc2[1][r]);
+          }
+        }
+    }
+    for (; jj < cnt; ++jj) {
+      const size_t base = (size_t)I0 * wc[jj];
+      const float za = va ? Z[base + i1a] : 0.f;
+      const float zb = vb ? Z[base + i1b] : 0.f;
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const float2 wv = ws[jj * RB + r];
+        acc1[0][r] = __fmaf_rn(za, wv.x, acc1[0][r]);
+        acc1[1][r] = __fmaf_rn(zb, wv.x, acc1[1][r]);
+        if (n != 0) {
+          acc2[0][r] = __fmaf_rn(za, wv.y, acc2[0][r]);
+          acc2[1][r] = __fmaf_rn(zb, wv.y, acc2[1][r]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (n == 0) {
+    float* Pp = reinterpret_cast<float*>(T.part[0]) + (size_t)u.k * I0 * kBR;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint32_t i1 = q ? i1b : i1a;
+      if (q ? vb : va)
+#pragma unroll
+        for (int r = 0; r < RB; ++r) Pp[(size_t)i1 * kBR + r] = acc1[q][r];
+    }
+  } else {
+    float t[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      float sum = 0.f;
+      if (r < R) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (!(q ? vb : va)) continue;
+          const size_t e = (q ? i1b : i1a) + (size_t)I0 * r;
+          const float ah = T.Ah[0][e], al = T.Al[0][e];
+          const float da = __fadd_rn(__fsub_rn(ah, T.Rh[0][e]), __fsub_rn(al, T.Rl[0][e]));
+          sum = __fmaf_rn(__fadd_rn(ah, al), acc1[q][r], sum);
+          sum = __fmaf_rn(da, acc2[q][r], sum);
+        }
+      }
+      t[r] = sum;
+    }
+    const float tot = warp_rs<RB>(t, lane);
+    constexpr int G = 32 / RB;
+    if (lane % G == 0) {
+      float* Pp = reinterpret_cast<float*>(T.part[n]) + ((size_t)u.in_idx * T.nk[n] + u.k) * kBR;
+      Pp[lane / G] = tot;
+    }
+  }
+}
+
 struct BSmem {
   double ws[kBWarps][32 * kBR];   // Khatri-Rao rows of 32 columns (float / double / float pairs)
   uint32_t wc[kBWarps][32];
@@ -437,6 +583,10 @@ __device__ void phase_units(const BArgs& a, int n, bool eval, BSmem& sm) {
     const int p = eval ? T.gprec : T.prec;
     if (T.zf64) unit_dispatch<BP_FP64, double>(T, u, lane, sm.ws[warp], sm.wc[warp]);
     else if (p == BP_FP32) unit_dispatch<BP_FP32, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+    else if (p == BP_DELTA) {
+      if (T.R <= 4) unit_run_delta<4>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+      else unit_run_delta<8>(T, u, lane, sm.ws[warp], sm.wc[warp]);
+    }
     else if (p == BP_DF) unit_dispatch<BP_DF, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
     else unit_dispatch<BP_FP64, float>(T, u, lane, sm.ws[warp], sm.wc[warp]);
   }
@@ -634,6 +784,18 @@ __device__ void row_one(const BTen& T, int n, int64_t i, int lane, bool update) 
         for (int k = 0; k < RB; ++k)
           if (k < R) x = __fma_rn(mk[k], T.ginv[k * kBR + lane], x);
         T.A[n][e] = x;
+      } else if constexpr (P == BP_DELTA) {
+        // M = M_ref + the FP32 correction, then A(i,:) = M Gamma^+ in float pairs
+        int64_t off = 0;
+        for (int q = 0; q < n; ++q) off += T.dims[q];
+        const double* mr = T.mref + (size_t)kBR * (off + i);
+        df x = {0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+          if (k < R) x = df_add(x, gi_mul(df_add(df_from_double(mr[k]), df{mk[k], 0.f}), T, k * kBR + lane));
+        T.A[n][e] = df_to_double(x);
+        T.Ah[n][e] = x.hi;
+        T.Al[n][e] = x.lo;
       } else {
         df x = {0.f, 0.f};
 #pragma unroll
@@ -657,6 +819,12 @@ __device__ void row_one(const BTen& T, int n, int64_t i, int lane, bool update) 
       res = d * d;
       mm = mr * mr;
       zi = mr * A[i + In * lane];
+      if (T.policy == CPMG_PREC_MIXED && T.shadow && (T.prec == BP_DF || T.prec == BP_DELTA) && !T.no_delta) {
+        // this evaluation's products become the reference of the delta sweeps that follow
+        int64_t off = 0;
+        for (int q = 0; q < n; ++q) off += T.dims[q];
+        T.mref[(size_t)kBR * (off + i) + lane] = mr;
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -695,11 +863,20 @@ __device__ void phase_rows(const BArgs& a, const BRow* items, int64_t nitems, bo
     const int p = update ? T.prec : T.gprec;
     if (T.zf64 || p == BP_FP64) row_dispatch<BP_FP64>(T, n, i, lane, update);
     else if (p == BP_DF) row_dispatch<BP_DF>(T, n, i, lane, update);
+    else if (p == BP_DELTA) row_dispatch<BP_DELTA>(T, n, i, lane, update);
     else row_dispatch<BP_FP32>(T, n, i, lane, update);
   }
 }
 
 __device__ void check_tensor(BTen& T, int* nactive, int launch_k, BSmem& sm) {
+  const bool take_ref =
+      T.policy == CPMG_PREC_MIXED && T.shadow && (T.prec == BP_DF || T.prec == BP_DELTA) && !T.no_delta;
+  if (take_ref)  // A_ref: the factors this evaluation's products (M_ref, stored by the rows) belong to
+    for (int m = 0; m < T.N; ++m)
+      for (int64_t e = threadIdx.x; e < T.dims[m] * T.R; e += blockDim.x) {
+        T.Rh[m][e] = T.Ah[m][e];
+        T.Rl[m][e] = T.Al[m][e];
+      }
   // sum over (r, c) of prod_n Upsilon^(n)_{rc} = ||[[A]]||^2, spread over threads
   double part = 0.0;
   for (int e = threadIdx.x; e < T.R * T.R; e += blockDim.x) {
@@ -759,7 +936,25 @@ __device__ void check_tensor(BTen& T, int* nactive, int launch_k, BSmem& sm) {
     } else {
       T.stall += 1;
     }
-    if (g < floor_g || T.stall >= 20) T.prec = BP_DF;
+    if (g < floor_g || T.stall >= 20) {
+      T.prec = BP_DF;
+      T.g_best = -1.0;
+      T.stall = 0;
+    }
+  } else if (take_ref) {
+    // refined: delta sweeps from the reference just taken, as long as they keep lowering g
+    if (T.g_best < 0 || g < T.g_best) {
+      T.g_best = g;
+      T.stall = 0;
+    } else {
+      T.stall += 1;
+    }
+    if (T.stall >= 3) {
+      T.no_delta = 1;
+      T.prec = BP_DF;
+    } else {
+      T.prec = BP_DELTA;
+    }
   }
   if (T.active) {
     // next interval: about half the sweeps the observed rate predicts are left, a power-of-two
@@ -1010,7 +1205,7 @@ static void plan_units(const std::vector<BItem>& items, std::vector<BUnit>* unit
 static size_t aux_doubles(const BItem& it) {
   int64_t rows = 0;
   for (int m = 0; m < it.N; ++m) rows += it.dims[m];
-  return (size_t)(2 * kBModes + 2) * kGramStride + (3 + kBR) * (size_t)rows;
+  return (size_t)(2 * kBModes + 2) * kGramStride + (3 + 3 * kBR) * (size_t)rows;
 }
 
 static size_t partial_doubles_of(const BItem& it) {
@@ -1046,6 +1241,12 @@ static BTen make_desc(const BItem& it) {
     T.Al[m] = m < it.N ? fb + kBR * it.dims[m] : nullptr;
     if (m < it.N) fb += 2 * kBR * it.dims[m];
   }
+  for (int m = 0; m < kBModes; ++m) {
+    T.Rh[m] = m < it.N ? fb : nullptr;
+    T.Rl[m] = m < it.N ? fb + kBR * it.dims[m] : nullptr;
+    if (m < it.N) fb += 2 * kBR * it.dims[m];
+  }
+  T.mref = reinterpret_cast<double*>(fb);
   T.N = it.N;
   T.R = it.R;
   T.zf64 = it.zf64;
@@ -1282,6 +1483,12 @@ struct BatchState {
     cpmg_result res;
     int state;     // 0 queued, 1 running, 2 done
     bool cancel = false;  // cpmg_server_cancel on a running request: retire at the next boundary
+    // a multilevel request (cpmg_server_submit_multilevel): the caller's buffers and options
+    bool ml = false;
+    cpmg_tensor z{};
+    int R = 0;
+    std::vector<double*> A, T;
+    cpmg_opts opts{};
     size_t bytes;  // HBM held while running (tensor, factors, partials, Gram)
   };
   std::mutex mu;
@@ -1297,6 +1504,11 @@ struct BatchState {
   size_t budget = 0, reserved = 0;
   int max_active = 1024;
   int sweeps_per_launch = 8;
+  // multilevel requests: their own queue, served by kMlWorkers threads with a context each
+  std::deque<Req*> ml_queue;
+  int ml_running = 0;
+  std::vector<std::thread> ml_workers;
+  bool ml_started = false;
   // failure-detection test hook (cpmg_debug_config): barrier wait limit, unreachable barrier
   double wait_limit_s = 2.0;
   int unreachable_barrier = 0;
@@ -1529,6 +1741,65 @@ static void server_loop(cpmg_ctx* c, BatchState* S) {
   S->cv.notify_all();
 }
 
+// ------------------------------------------------------------------ multilevel request workers
+constexpr int kMlWorkers = 2;
+
+// One multilevel request at a time, by the "Multilevel" driver of Section 6.1 (cpmg_decompose) on
+// a context and stream of the worker's own: the request's hierarchy is allocated when it starts
+// and released when it ends, its launches overlap the batched worker's, and its arithmetic does
+// not depend on what else runs.  Admission shares the server's HBM budget.
+static void ml_loop(cpmg_ctx* parent, BatchState* S) {
+  const int dev = ctx_device(parent);
+  cudaSetDevice(dev);
+  cudaStream_t st = nullptr;
+  cpmg_ctx* c2 = nullptr;
+  int rc = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? CPMG_OK : CPMG_CUDA_ERROR;
+  if (rc == CPMG_OK) rc = cpmg_create(&c2, dev, 0, st);
+  while (true) {
+    BatchState::Req* q = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      while (!S->stop && (S->ml_queue.empty() || (S->budget && S->reserved + S->ml_queue.front()->bytes > S->budget &&
+                                                   (S->reserved > 0))))
+        S->cv.wait_for(lk, std::chrono::milliseconds(5));
+      if (S->stop) break;
+      q = S->ml_queue.front();
+      S->ml_queue.pop_front();
+      q->state = 1;
+      S->reserved += q->bytes;
+      S->ml_running += 1;
+    }
+    cpmg_result r;
+    std::memset(&r, 0, sizeof(r));
+    int s = rc;
+    if (s == CPMG_OK) s = cpmg_decompose(c2, &q->z, q->R, q->A.data(), q->T.empty() ? nullptr : q->T.data(), &q->opts, &r);
+    const auto now = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(S->mu);
+    q->res = r;
+    if (s != CPMG_OK && s != CPMG_NOT_CONVERGED) q->res.status = s;
+    const double lat = std::chrono::duration<double>(now - q->t_submit).count();
+    q->res.seconds = lat;
+    q->t_done = now;
+    q->state = 2;
+    S->reserved -= q->bytes;
+    S->ml_running -= 1;
+    S->lat.push_back(lat);
+    S->completed += 1;
+    S->t_last = now;
+    S->cv.notify_all();
+  }
+  if (c2) cpmg_destroy(c2);
+  if (st) cudaStreamDestroy(st);
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (auto* q : S->ml_queue) {  // not started: fail them so that pollers do not wait forever
+    std::memset(&q->res, 0, sizeof(q->res));
+    q->res.status = CPMG_CANCELLED;
+    q->state = 2;
+  }
+  S->ml_queue.clear();
+  S->cv.notify_all();
+}
+
 void batch_state_destroy(cpmg_ctx* c) {
   BatchState*& s = ctx_batch_state(c);
   if (!s) return;
@@ -1538,6 +1809,8 @@ void batch_state_destroy(cpmg_ctx* c) {
   }
   s->cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  for (auto& w : s->ml_workers)
+    if (w.joinable()) w.join();
   for (auto& kv : s->reqs) delete kv.second;
   delete s;
   s = nullptr;
@@ -1757,9 +2030,10 @@ int cpmg_server_cancel(cpmg_ctx* c, uint64_t ticket) {
   if (f == S->reqs.end()) return CPMG_INVALID_ARG;
   BatchState::Req* q = f->second;
   if (q->state == 0) {  // still queued: leaves the queue now, its factors untouched
-    for (auto it = S->queue.begin(); it != S->queue.end(); ++it)
+    auto& qu = q->ml ? S->ml_queue : S->queue;
+    for (auto it = qu.begin(); it != qu.end(); ++it)
       if (*it == q) {
-        S->queue.erase(it);
+        qu.erase(it);
         break;
       }
     std::memset(&q->res, 0, sizeof(q->res));
@@ -1767,9 +2041,9 @@ int cpmg_server_cancel(cpmg_ctx* c, uint64_t ticket) {
     q->res.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - q->t_submit).count();
     q->state = 2;
     S->cv.notify_all();
-  } else if (q->state == 1) {
+  } else if (q->state == 1 && !q->ml) {
     q->cancel = true;  // the worker retires it after the launch in flight
-  }
+  }  // a running multilevel request is one solver call: it finishes
   return CPMG_OK;
 }
 
@@ -1825,9 +2099,70 @@ int cpmg_server_submit(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* 
     S->any = true;
     S->t_first = q->t_submit;
   }
-  if (!S->started) {
+  if (!S->worker.joinable()) {
     S->started = true;
     S->worker = std::thread(server_loop, c, S);
+  }
+  *ticket = q->id;
+  lk.unlock();
+  S->cv.notify_all();
+  return CPMG_OK;
+}
+
+int cpmg_server_submit_multilevel(cpmg_ctx* c, const cpmg_tensor* Z, int R, double* const* A,
+                                  double* const* A_test, const cpmg_opts* opts, uint64_t* ticket) {
+  if (!c || !ticket || !Z || !A || !opts || !Z->data) return CPMG_INVALID_ARG;
+  if (Z->N < 2 || Z->N > CPMG_MAX_MODES || Z->mem != CPMG_MEM_DEVICE || R < 1 || R > CPMG_MAX_RANK)
+    return CPMG_INVALID_ARG;
+  if (opts->n_t < 0 || opts->n_t > CPMG_MAX_TEST_BLOCKS || (opts->n_t > 0 && !A_test)) return CPMG_INVALID_ARG;
+  auto* q = new BatchState::Req();
+  q->ml = true;
+  q->z = *Z;
+  q->R = R;
+  q->opts = *opts;
+  int64_t P = 1;
+  size_t fb = 0;
+  for (int m = 0; m < Z->N; ++m) {
+    if (Z->dims[m] < 1 || !A[m]) {
+      delete q;
+      return CPMG_INVALID_ARG;
+    }
+    P *= Z->dims[m];
+    fb += (size_t)Z->dims[m] * R * 8;
+    q->A.push_back(A[m]);
+  }
+  for (int t = 0; t < opts->n_t; ++t)
+    for (int m = 0; m < Z->N; ++m) {
+      if (!A_test[t * Z->N + m]) {
+        delete q;
+        return CPMG_INVALID_ARG;
+      }
+      q->T.push_back(A_test[t * Z->N + m]);
+    }
+  std::memset(&q->item, 0, sizeof(q->item));
+  q->state = 0;
+  q->t_submit = std::chrono::steady_clock::now();
+  // HBM held while it runs: the coarse tensors (under 1/7 of Z for third order, more for lower
+  // orders: counted as one more Z), the MTTKRP scratch (about one more Z), the factor sets
+  const size_t zb = (size_t)P * (Z->dtype == CPMG_F64 ? 8 : 4);
+  q->bytes = zb + zb + 2 * zb + fb * (size_t)(2 * opts->n_t + 8) + ((size_t)64 << 20);
+  BatchState* S = state_of(c);
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->budget && q->bytes > S->budget) {
+    delete q;
+    return CPMG_OUT_OF_BUDGET;
+  }
+  q->id = S->next_id++;
+  S->reqs[q->id] = q;
+  S->ml_queue.push_back(q);
+  if (!S->any) {
+    S->any = true;
+    S->t_first = q->t_submit;
+  }
+  if (!S->ml_started) {
+    S->ml_started = true;
+    S->started = true;  // the context now serves: other solver calls are refused
+    for (int w = 0; w < kMlWorkers; ++w) S->ml_workers.emplace_back(ml_loop, c, S);
   }
   *ticket = q->id;
   lk.unlock();
@@ -1854,7 +2189,7 @@ int cpmg_server_wait(cpmg_ctx* c, double timeout_s) {
   BatchState* S = state_of(c);
   std::unique_lock<std::mutex> lk(S->mu);
   const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
-  while (!S->queue.empty() || !S->active.empty()) {
+  while (!S->queue.empty() || !S->active.empty() || !S->ml_queue.empty() || S->ml_running > 0) {
     if (S->cv.wait_until(lk, deadline) == std::cv_status::timeout) return CPMG_PENDING;
   }
   return S->worker_status;
