@@ -1140,7 +1140,7 @@ static int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // at 2k).  The switch depends only on the tensor's own sweep count, so its arithmetic is the same
 // alone, in any batch, and in the server.
 constexpr int kLateSweeps = 512;
-constexpr int64_t kLateUnit = 2048;
+constexpr int64_t kLateUnit = 4096;
 
 // Marks the loaded tensors that crossed kLateSweeps; true when any unit list must be rebuilt.
 static bool late_switch(std::vector<BItem*>& items, const std::vector<BTen>& host) {

@@ -331,3 +331,22 @@ def test_split_bf16_sweeps_match_oracle(cpmg_ctx):
     assert r["status"] == cpmg.OK and T.g_value(Z64, host(cpmg, A)) < 1e-10
     ref_c, _ = ALS.als(Z64, p.A0, 5000, tol=1e-10, g_fn=T.g_value)
     assert_same_stationary_point(Z64, host(cpmg, A), ref_c, 1e-10)
+
+
+def test_dimension_tree_w_pass_large_fp32(cpmg_ctx):
+    """A tensor with enough rows (400 x 400 x 64) for the W pass's four-rows-per-thread, packed-FMA
+    variant: one FP32 sweep with the tree matches the sweep without it and the oracle's ALS."""
+    from paper_1111_6091_gb300 import cpmg
+    p = synth.make_problem((400, 400, 64), 10, congruence=0.5, eta_homo=0.01, dtype=np.float32, seed=8, n_t=0)
+    Z64 = p.Z.astype(np.float64)
+    ref = ALS.sort_components(ALS.als_sweep(Z64, p.A0))
+    out = []
+    for tree in (1, 0):
+        A = dev(cpmg, p.A0)
+        cpmg.cp_als_sweep(cpmg_ctx, cpmg.colmajor(p.Z), A, 1, precision=cpmg.PREC_FP32, check_every=0,
+                          dimension_tree=tree)
+        out.append(host(cpmg, A))
+        for a, b in zip(out[-1], ref):
+            assert np.max(np.abs(a - b)) <= 2e-4 * np.max(np.abs(b)), tree
+    for a, b in zip(*out):
+        assert np.max(np.abs(a - b)) <= 2e-4 * np.max(np.abs(b))
