@@ -956,6 +956,13 @@ __device__ void check_tensor(BTen& T, int* nactive, int launch_k, BSmem& sm) {
       T.prec = BP_DELTA;
     }
   }
+  if (T.active && T.policy == CPMG_PREC_MIXED) {
+    // the next check's g: FP32 products while the tensor sweeps in FP32 and g is more than 64 times
+    // its FP32 floor (the rounding is then a few percent of g at most); float-pair accurate from
+    // there on, so the switch and the stopping test always see an accurate g
+    const double floor_g = T.mixed_switch * 5.960464477539063e-08 * sqrt(m2) / zn;
+    T.gprec = (T.prec == BP_FP32 && g > 64.0 * floor_g) ? BP_FP32 : BP_DF;
+  }
   if (T.active) {
     // next interval: about half the sweeps the observed rate predicts are left, a power-of-two
     // multiple of the launch's sweeps, at most 32 (and the launch's sweeps while g is not falling)
@@ -1258,7 +1265,8 @@ static BTen make_desc(const BItem& it) {
     T.gprec = BP_FP64;
   } else {
     T.prec = (it.o.precision == CPMG_PREC_DF) ? BP_DF : BP_FP32;
-    T.gprec = BP_DF;
+    // MIXED starts far above the FP32 floor: its first checks evaluate g with FP32 products
+    T.gprec = it.o.precision == CPMG_PREC_MIXED ? BP_FP32 : BP_DF;
   }
   T.active = 1;
   T.init = 1;
