@@ -73,9 +73,10 @@ __global__ void __launch_bounds__(256) k_dt_mode1(const TW* __restrict__ W, int6
 // ------------------------------------------------------------------ W = X C (one pass over X)
 constexpr int kWThreads = 128;
 constexpr int kWTile = 256;    // columns of C staged in shared memory at a time
-// columns of X whose loads are in flight together: FP32 keeps 16 (the bytes in flight per SM set
-// the streaming rate); the float-pair and float64 accumulators leave registers for 8
-constexpr int w_unroll(int prec) { return prec == P_FP32 ? 16 : 8; }
+// columns of X whose loads are in flight together: FP32 keeps 32 (two rows per thread) or 16 (four
+// rows): the bytes in flight per SM set the streaming rate; the float-pair and float64
+// accumulators leave registers for 8
+constexpr int w_unroll(int prec, int vw) { return prec == P_FP32 ? (vw <= 2 ? 32 : 16) : 8; }
 
 // accumulation per precision: FP32 fma; float pairs (the product's error and the TwoSum error of
 // the running sum go to the low word, folded back after every group of columns); float64 fma
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(kWThreads) k_dt_w(const TZ* __restrict__ X, in
     if (!live) continue;
     const TZ* xp = X + p0 + P * k0;
     int kk = 0;
-    constexpr int U = w_unroll(PREC);
+    constexpr int U = w_unroll(PREC, VW);
     for (; kk + U <= kt; kk += U) {
       WVec<TZ, VW> x[U];
 #pragma unroll
@@ -237,7 +238,10 @@ int launch_dt_w(const void* X, int zdtype, int64_t P, int64_t K, int R, const do
     else v2 ? launch_w_rp<double, P_FP64, 2>(x, P, K, R, C, W, st) : launch_w_rp<double, P_FP64, 1>(x, P, K, R, C, W, st);
   } else {
     const float* x = static_cast<const float*>(X);
-    const int vw = fits(4, 16) ? 4 : fits(2, 8) ? 2 : 1;
+    // two rows per thread when that still gives about four CTAs per SM: twice the resident warps
+    // of four rows per thread for the same bytes in flight
+    const bool v2many = P % 2 == 0 && xa % 8 == 0 && (P / 2 + kWThreads - 1) / kWThreads >= 4 * (int64_t)num_sms;
+    const int vw = v2many ? 2 : fits(4, 16) ? 4 : fits(2, 8) ? 2 : 1;
     switch (prec) {
       case P_FP32:
         vw == 4 ? launch_w_rp<float, P_FP32, 4>(x, P, K, R, C, W, st)
