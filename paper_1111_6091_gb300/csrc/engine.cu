@@ -1122,6 +1122,8 @@ static Solver make_solver(cpmg_ctx* c, const cpmg_opts* o) {
   // stream capture is not available on the legacy default stream
   S.use_graphs = o->use_graphs != 0 && c->stream != nullptr;
   S.ttm_tc = o->ttm_tensor_cores ? 1 : 0;
+  // the timeout flag of an earlier call that gave up is not this call's
+  cudaMemsetAsync(c->dstatus + 1, 0, sizeof(int), c->stream);
   return S;
 }
 
@@ -1332,6 +1334,8 @@ int cpmg_ttm(cpmg_ctx* c, const cpmg_tensor* Z, const double* const* Rhat, const
   if (st == CPMG_OK && tensor_cores) st = dalloc(c, &tcs, ttm_tc_scratch_bytes(imax));
   cudaEvent_t ev[2 * kMaxModes];
   if (st == CPMG_OK) st = prof_ttm(c, s, Z->dtype, Rh, icv, tensor_cores, ev);
+  if (st == CPMG_OK && cudaMemsetAsync(c->dstatus + 1, 0, sizeof(int), c->stream) != cudaSuccess)
+    st = CPMG_CUDA_ERROR;
   if (st == CPMG_OK)
     st = ttm_restrict(s, Z->data, Z->dtype, Rh, icv, Y, t0, t1, tensor_cores ? 2 : 0, tcs, c->dstatus + 1, ev,
                       false, c->stream);

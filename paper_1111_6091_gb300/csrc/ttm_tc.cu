@@ -2,23 +2,29 @@
 //
 // Each mode product is a GEMM whose tensor-core M dimension is a large index of Z and whose
 // N dimension is the coarse size Ic (<= 256), with L = prod_{m<n} I_m, G = prod_{m>n} I_m:
-//   n = 1 : Y(c, g)    = sum_k R-hat(c, k) Z(k, g)     D(g, c), A = Z tile (K-major)
-//   n > 1 : Y(l, c, g) = sum_k Z(l, k, g) R-hat(c, k)  D(l, c), A = Z tile (MN-major), per g
-// B is R-hat with c contiguous (MN-major) in both cases.
+//   n = 1 : Y(c, g)    = sum_k R-hat(c, k) Z(k, g)     D(g, c), A(g, k) = Z(k, g)
+//   n > 1 : Y(l, c, g) = sum_k Z(l, k, g) R-hat(c, k)  D(l, c), A(l, k) = Z(l, k, g), per g
+// B is R-hat with c contiguous (MN-major) in shared memory.
 //
 // Precision (split BF16): every float x is hi + lo with hi = bf16(x), lo = bf16(x - hi).  The
 // products hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor memory; the dropped lo*lo
 // term and the rounding of lo leave a relative error near 2^-16 per product.
 //
+// The A operand lives in tensor memory.  Splitter threads own one row of the 128-row tile each
+// (its tensor-memory lane), split its 16 k values of a half stage and write hi and lo with
+// tcgen05.st; the MMA reads A from there and only B from shared memory.  Shared memory carries
+// the fp32 tiles of Z (written by TMA, read once by the splitters) and a ring of pre-split
+// R-hat chunks, so per 32-wide K step it moves about 16 + 16 + 26 + 40 KB (Ic = 200) instead of
+// also writing the split A tile and reading it three times.
+//
 // Persistent CTAs of 480 threads, one per SM, walk 128-row output tiles:
 //   warp 0      producer: fp32 tiles of Z by cp.async.bulk.tensor (128-byte swizzle)
-//   warps 1..8  split the fp32 tile into BF16 hi / lo in the canonical no-swizzle core-matrix
-//               layout (or load it straight from global memory when the tensor's strides do
-//               not suit a tensor map)
-//   warp 9      allocates tensor memory (two accumulators of 256 columns); one lane issues
-//               tcgen05.mma into the accumulator of the current tile
-//   warps 10-13 drain the other accumulator into Y while the next tile is computed
-//   warp 14     producer: pre-split R-hat chunks by cp.async.bulk
+//   warp 1      producer: pre-split R-hat chunks by cp.async.bulk, in a ring of their own
+//   warp 2      allocates tensor memory; one lane issues tcgen05.mma (A from tensor memory)
+//   warps 3-10  splitters: two per lane quarter, one per half of the 32-wide K step (or
+//               loading Z straight from global memory when its strides do not suit a tensor map)
+//   warps 11-14 drain an accumulator into Y while the next tile is computed (two accumulators
+//               when they leave room for four A stages, else one)
 // Every mbarrier wait gives up after about 2 s, records an error and lets the CTA unwind.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -34,18 +40,23 @@ namespace cpmg {
 
 namespace {
 
-constexpr int BMT = 128;      // tensor-core M tile (TMEM lanes)
-constexpr int BKT = 32;       // K per pipeline stage (two MMA K steps)
-constexpr int kConvWarps = 8;                   // warps splitting fp32 -> BF16 (warps 1..8)
-constexpr int kMmaWarp = 1 + kConvWarps;        // tensor-memory owner and MMA issuer
-constexpr int kEpiWarp0 = kMmaWarp + 1;         // four epilogue warps
-constexpr int kBWarp = kEpiWarp0 + 4;           // R-hat chunk producer
-constexpr int THREADS = 32 * (kBWarp + 1);
-constexpr int kUnitsPerThread = 512 / (32 * kConvWarps);  // 16-byte core-matrix rows per stage
-constexpr int kTmemCols = 256;
-constexpr uint32_t kF32Bytes = BMT * BKT * 4;   // fp32 staging of one stage
-constexpr uint32_t kAHalf = BMT * BKT * 2;      // one BF16 term of A
-constexpr int kStageBase = 1024;                // 128-byte swizzle wants 1 KB alignment
+constexpr int BMT = 128;                       // tensor-core M tile (TMEM lanes)
+constexpr int BKT = 32;                        // K per pipeline stage (two MMA K steps)
+constexpr int kZWarp = 0;                      // fp32 Z tile producer
+constexpr int kBWarp = 1;                      // R-hat chunk producer
+constexpr int kMmaWarp = 2;                    // tensor-memory owner and MMA issuer
+constexpr int kSplitWarp0 = 3;                 // splitter warps: kGroups groups of four
+constexpr int kGroups = 4;
+constexpr int kSplitWarps = 4 * kGroups;
+constexpr int kEpiWarp0 = kSplitWarp0 + kSplitWarps;  // four epilogue warps
+constexpr int THREADS = 32 * (kEpiWarp0 + 4);
+constexpr int kTmemCols = 512;                 // the whole of an SM's tensor memory
+constexpr int kAccStride = 256;                // second accumulator's first column
+constexpr int kAStageCols = 16;                // per K16 half-step: hi (8 columns), lo (8 columns)
+constexpr int kMaxAStages = 8;
+constexpr int kMaxRing = 8;
+constexpr uint32_t kF32Bytes = BMT * BKT * 4;  // fp32 staging of one stage
+constexpr int kStageBase = 1024;               // 128-byte swizzle wants 1 KB alignment
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -65,15 +76,43 @@ __device__ __forceinline__ bool bar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait: false after ~2 s without the phase completing
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+
+__device__ __forceinline__ bool failed(const int* fail) { return *reinterpret_cast<const volatile int*>(fail) != 0; }
+
+// bounded wait: false after ~2 s without the phase completing, or once another role of the
+// CTA has recorded a failure in *fail (fail null: only the phase or the time limit ends it)
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, const int* fail) {
   if (bar_try(bar, parity)) return true;
   const uint64_t t0 = gtime();
   while (true) {
     if (bar_try(bar, parity)) return true;
-    if (gtime() - t0 > 2000000000ull) return false;
+    if ((fail && failed(fail)) || gtime() - t0 > 2000000000ull) return false;
   }
 }
+
+// the same for a whole warp: lane 0 polls the barrier (32 lanes polling one mbarrier would
+// queue 32 shared-memory operations per test), then the warp synchronizes, which orders the
+// other lanes' later reads after lane 0's observation of the phase
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, const int* fail) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = bar_wait(bar, parity, fail) ? 1 : 0;
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// cursor over a ring of S slots: the slot, and the parity of the phase its current use
+// completes (no divisions in the loops)
+struct Ring {
+  int slot, S;
+  uint32_t phase;
+  __device__ explicit Ring(int s) : slot(0), S(s), phase(0) {}
+  __device__ void next() {
+    if (++slot == S) {
+      slot = 0;
+      phase ^= 1u;
+    }
+  }
+};
 
 __device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
@@ -86,6 +125,10 @@ __device__ __forceinline__ void bar_arrive_tx(uint64_t* bar, uint32_t bytes) {
                "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
 
 // shared-memory matrix descriptor: start, leading / stride byte offsets, tcgen05 version,
 // no swizzle
@@ -94,26 +137,53 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-               "l"(da), "l"(db), "r"(idesc), "r"(acc)
+// One K16 half-step of split BF16: D [+]= A_hi B_hi + A_hi B_lo + A_lo B_hi, A in tensor memory,
+// B in shared memory.  The same instruction block tests (without blocking) whether phase p0 of
+// barrier b0 and phase p1 of b1 have completed, so that the latency of those tests overlaps
+// the issue of the three MMAs; bit 0 / bit 1 of the result report them.
+__device__ __forceinline__ uint32_t mma3_test(uint32_t d, uint32_t ahi, uint32_t alo, uint64_t dBh, uint64_t dBl,
+                                              uint32_t idesc, uint32_t acc, const uint64_t* b0, uint32_t p0,
+                                              const uint64_t* b1, uint32_t p1) {
+  uint32_t r0, r1;
+  asm volatile(
+      "{\n\t.reg .pred pa, pt, q0, q1;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q0, [%9], %10;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q1, [%11], %12;\n\t"
+      "setp.ne.b32 pa, %8, 0;\n\t"
+      "setp.eq.b32 pt, %8, %8;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%3], %5, %7, pa;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%3], %6, %7, pt;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%4], %5, %7, pt;\n\t"
+      "selp.u32 %0, 1, 0, q0;\n\t"
+      "selp.u32 %1, 1, 0, q1;\n\t}"
+      : "=r"(r0), "=r"(r1)
+      : "r"(d), "r"(ahi), "r"(alo), "l"(dBh), "l"(dBl), "r"(idesc), "r"(acc), "r"(su32(b0)), "r"(p0),
+        "r"(su32(b1)), "r"(p1)
+      : "memory");
+  return r0 | (r1 << 1);
+}
+
+// eight 32-bit columns of this warp's 32 tensor-memory lanes (lane i of the warp writes lane
+// base + i)
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
                : "memory");
 }
 
-// x -> (hi, lo) for 8 floats, packed as bf16 pairs
-__device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
+// x -> (hi, lo) for 16 floats; column j packs elements 2j (low half) and 2j + 1 (high half),
+// the order of consecutive K elements in memory.  Two floats per conversion instruction; a
+// BF16 value widens to float exactly by a 16-bit shift.
+__device__ __forceinline__ void split16(const float* x, uint32_t* hi, uint32_t* lo) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]), h1 = __float2bfloat16_rn(x[2 * i + 1]);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
-    h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-    l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  for (int j = 0; j < 8; ++j) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+    const uint32_t hb = *reinterpret_cast<const uint32_t*>(&h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x[2 * j] - __uint_as_float(hb << 16),
+                                                   x[2 * j + 1] - __uint_as_float(hb & 0xffff0000u));
+    hi[j] = hb;
+    lo[j] = *reinterpret_cast<const uint32_t*>(&l);
   }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // byte offset of 16-byte chunk `chunk` of 128-byte row `row` under the 128-byte swizzle
@@ -122,9 +192,12 @@ __device__ __forceinline__ uint32_t sw128(int row, int chunk) {
 }
 
 struct TcArgs {
-  int first;            // 1: mode 1 (A K-major), 0: later mode (A MN-major)
-  int direct;           // 1: converters load Z from global memory (no tensor map)
-  int sf, sm;           // slots of the fp32 ring and of the MMA-operand ring
+  int first;            // 1: mode 1 (rows of A are g, k contiguous), 0: later mode (rows are l)
+  int direct;           // 1: splitters load Z from global memory (no tensor map)
+  int btm;              // 1: R-hat chunks through their tensor map (rows of 128 bytes), else bulk copies
+  int sf, sb, sa;       // slots of the fp32 ring, of the R-hat ring, K16 A stages in tensor memory
+  int nacc;             // accumulators in tensor memory: 1 (at column 0) or 2 (at 0 and 256)
+  int n0;               // A stages after the first accumulator; the rest follow the second
   int64_t M, K, Ic;     // GEMM sizes: spatial rows, contracted index, coarse size
   int Npad;             // Ic rounded up to a multiple of 16
   int64_t batch;        // G for a later mode, 1 for mode 1
@@ -139,51 +212,59 @@ struct TcArgs {
   int* err;
 };
 
-__device__ __forceinline__ bool failed(const int* fail) { return *reinterpret_cast<const volatile int*>(fail) != 0; }
 
-// Persistent: CTA b handles tiles b, b + gridDim.x, ...  Two rings of shared memory: fp32 tiles
-// of Z (freed as soon as they are split, so Z loads run several stages ahead) and MMA operands
-// (BF16 hi / lo of the Z tile and the R-hat chunk, freed by the MMA commit).  Two tensor-memory
-// accumulators let the epilogue of one tile overlap the main loop of the next.
-__global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+// Persistent: CTA b handles tiles b, b + gridDim.x, ...  Three rings: fp32 tiles of Z in shared
+// memory (freed as soon as they are split, so Z loads run several stages ahead), R-hat chunks
+// in shared memory and A stages in tensor memory (both freed by the MMA commit).  With two
+// accumulators the epilogue of one tile overlaps the main loop of the next.
+__global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ CUtensorMap tmap,
+                                                        const __grid_constant__ CUtensorMap bmap, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int SF = a.sf, SM = a.sm;
+  const int SF = a.sf, SB = a.sb, SA = a.sa, NA = a.nacc;
+  // first tensor-memory column of K16 A stage s: the columns after each accumulator
+  auto stage_col = [&](int s) -> uint32_t {
+    return (uint32_t)(s < a.n0 ? a.Npad + kAStageCols * s : kAccStride + a.Npad + kAStageCols * (s - a.n0));
+  };
   uint64_t* ffull = reinterpret_cast<uint64_t*>(smem);  // fp32 tile landed
-  uint64_t* fempty = ffull + 8;                          // fp32 tile read by the splitters
-  uint64_t* mfull = fempty + 8;                          // R-hat chunk landed (slot claimed)
-  uint64_t* conv = mfull + 8;                            // BF16 split written
-  uint64_t* mempty = conv + 8;                           // MMAs reading the slot completed
-  uint64_t* tfull = mempty + 8;                          // [2] accumulator complete
-  uint64_t* tempty = tfull + 2;                          // [2] accumulator drained
+  uint64_t* fempty = ffull + kMaxRing;                  // fp32 tile read by the splitters
+  uint64_t* bfull = fempty + kMaxRing;                  // R-hat chunk landed
+  uint64_t* kempty = bfull + kMaxRing;                  // MMAs of a K step completed: its R-hat
+                                                        // slot and A stage pair are free
+  uint64_t* afull = kempty + kMaxRing;                  // A stage written to tensor memory
+  uint64_t* tfull = afull + kMaxAStages;                // [2] accumulator complete
+  uint64_t* tempty = tfull + 2;                         // [2] accumulator drained
+  uint64_t* mdone = tempty + 2;                         // every MMA issued has completed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 512);
   int* fail = reinterpret_cast<int*>(smem + 520);
-  const uint32_t mslot = 2 * kAHalf + 2 * a.bchunk;
   unsigned char* fring = smem + kStageBase;
-  unsigned char* mring = fring + (size_t)SF * kF32Bytes;
+  unsigned char* bring = fring + (size_t)SF * kF32Bytes;
+  const uint32_t bslot = 2 * a.bchunk;
   const int nk = (int)((a.K + BKT - 1) / BKT);
-  const uint32_t a_lbo = a.first ? 128u : (uint32_t)(BMT / 8) * 128u;
-  const uint32_t a_sbo = a.first ? (uint32_t)(BKT / 8) * 128u : 128u;
+  // CTAs start their K loops at different chunks, so that the SMs do not all read the same
+  // R-hat chunk at the same moment
+  const int rot = (int)(blockIdx.x % nk);
   const uint32_t b_lbo = (uint32_t)(a.Npad / 8) * 128u, b_sbo = 128u;
 
   if (t == 0) {
-    for (int s = 0; s < 8; ++s) {
+    for (int s = 0; s < kMaxRing; ++s) {
       bar_init(&ffull[s], 1);
-      bar_init(&fempty[s], kConvWarps);
-      bar_init(&mfull[s], 1);
-      bar_init(&conv[s], kConvWarps);
-      bar_init(&mempty[s], 1);
+      bar_init(&fempty[s], 8);  // the two half-steps of a stage, four warps each
+      bar_init(&bfull[s], 1);
+      bar_init(&kempty[s], 1);
     }
+    for (int s = 0; s < kMaxAStages; ++s) bar_init(&afull[s], 4);
     for (int j = 0; j < 2; ++j) {
       bar_init(&tfull[j], 1);
       bar_init(&tempty[j], 4);
     }
+    bar_init(mdone, 1);
     *fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                 "r"(2 * kTmemCols)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -192,34 +273,33 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  if (warp == 0 || warp == kBWarp) {
+  if (warp == kZWarp || warp == kBWarp) {
     // ------------------------------------------------------------ producers
-    // warp 0: fp32 tiles of Z (tensor map); warp 10: R-hat chunks into the operand ring
-    const bool zp = warp == 0;
+    const bool zp = warp == kZWarp;
     if (lane == 0 && !(zp && a.direct)) {
-      const int S = zp ? SF : SM;
-      uint64_t* fullb = zp ? ffull : mfull;
-      uint64_t* emptyb = zp ? fempty : mempty;
-      int it = 0;
+      const int S = zp ? SF : SB;
+      uint64_t* fullb = zp ? ffull : bfull;
+      uint64_t* emptyb = zp ? fempty : kempty;
+      Ring r(S);
+      int it = 0, kq = rot;
       for (int64_t tile = blockIdx.x; tile < a.ntiles && !failed(fail); tile += gridDim.x) {
         const int64_t b = tile / a.mtiles;
         const int m0 = (int)((tile % a.mtiles) * BMT);
         for (int kc = 0; kc < nk; ++kc, ++it) {
-          const int s = it % S;
-          if (it >= S && !bar_wait(&emptyb[s], (uint32_t)(((it / S) - 1) & 1))) {
+          if (it >= S && !bar_wait(&emptyb[r.slot], r.phase ^ 1u, fail)) {
             atomicOr(fail, 1);
             break;
           }
-          const int k0 = kc * BKT;
+          const int k0 = kq * BKT;
           if (zp) {
-            unsigned char* st = fring + (size_t)s * kF32Bytes;
-            bar_arrive_tx(&fullb[s], kF32Bytes);
+            unsigned char* st = fring + (size_t)r.slot * kF32Bytes;
+            bar_arrive_tx(&fullb[r.slot], kF32Bytes);
             if (a.first) {
               // box {BKT along k, BMT along g}: 128 rows of 128 bytes
               asm volatile(
                   "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
                   "[%4];" ::"r"(su32(st)),
-                  "l"(&tmap), "r"(k0), "r"(m0), "r"(su32(&fullb[s]))
+                  "l"(&tmap), "r"(k0), "r"(m0), "r"(su32(&fullb[r.slot]))
                   : "memory");
             } else {
               // four boxes {32 along l, BKT along k, 1}: each 32 rows (k) of 128 bytes (l)
@@ -227,178 +307,208 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
                 asm volatile(
                     "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
                     "%4}], [%5];" ::"r"(su32(st + q * 4096)),
-                    "l"(&tmap), "r"(m0 + 32 * q), "r"(k0), "r"((int)b), "r"(su32(&fullb[s]))
+                    "l"(&tmap), "r"(m0 + 32 * q), "r"(k0), "r"((int)b), "r"(su32(&fullb[r.slot]))
                     : "memory");
             }
           } else {
-            unsigned char* st = mring + (size_t)s * mslot;
-            bar_arrive_tx(&fullb[s], 2 * a.bchunk);
-            const unsigned char* src = a.bsplit + (size_t)kc * 2 * a.bchunk;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    su32(st + 2 * kAHalf)),
-                "l"(src), "r"(2 * a.bchunk), "r"(su32(&fullb[s]))
-                : "memory");
+            unsigned char* st = bring + (size_t)r.slot * bslot;
+            bar_arrive_tx(&fullb[r.slot], bslot);
+            if (a.btm) {
+              // box {64 BF16, Npad rows}: the chunk's Npad rows of 128 bytes, in order
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                  "[%4];" ::"r"(su32(st)),
+                  "l"(&bmap), "r"(0), "r"(kq * a.Npad), "r"(su32(&fullb[r.slot]))
+                  : "memory");
+            } else {
+              const unsigned char* src = a.bsplit + (size_t)kq * bslot;
+              asm volatile(
+                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                      su32(st)),
+                  "l"(src), "r"(bslot), "r"(su32(&fullb[r.slot]))
+                  : "memory");
+            }
+          }
+          r.next();
+          if (++kq == nk) kq = 0;
+        }
+      }
+      // the CTA may not exit while a copy is still in flight (this wait ignores the failure
+      // flag: only the copy's own completion, or the time limit, ends it)
+      for (int j = (it > S ? it - S : 0); j < it; ++j)
+        if (!bar_wait(&fullb[j % S], (uint32_t)((j / S) & 1), nullptr)) atomicOr(fail, 1);
+    }
+  } else if (warp >= kSplitWarp0 && warp < kEpiWarp0) {
+    // ------------------------------------------------------------ split fp32 -> BF16 hi / lo
+    // Half-step hs = 2 it + h covers k = 16 h .. 16 h + 15 of K step `it`.  Group g (four
+    // warps, one per lane quarter) takes half-steps g, g + kGroups, ..., so that kGroups
+    // half-steps are in flight at once.  A thread owns row 32 q + lane of the tile (its
+    // tensor-memory lane); hi goes to the 8 columns of its A stage, lo to the next 8.
+    const int q = warp & 3, g = (warp - kSplitWarp0) >> 2;
+    const int r = 32 * q + lane;
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    // cursors for half-step hs: K step it = hs / 2 (tile tile_i = it / nk, chunk kc = it % nk),
+    // fp32 slot it % SF, A stage pair it % SB (stage 2 pair + h)
+    int hs = g, it = g >> 1, kc = it, kq = 0;
+    int64_t tile = blockIdx.x;
+    while (kc >= nk) {
+      kc -= nk;
+      tile += gridDim.x;
+    }
+    kq = kc + rot;
+    if (kq >= nk) kq -= nk;
+    int fslot = 0, pslot = it % SB;
+    uint32_t fph = 0, pph = (uint32_t)((it / SB) & 1);
+    if (SF > 0) {
+      fslot = it % SF;
+      fph = (uint32_t)((it / SF) & 1);
+    }
+    while (tile < a.ntiles) {
+      const int h = hs & 1;
+      const int64_t b = tile / a.mtiles;
+      const int64_t m = (tile % a.mtiles) * BMT + r;
+      const int64_t k0 = (int64_t)kq * BKT + 16 * h;
+      float x[16];
+      if (a.direct) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int64_t k = k0 + i;
+          x[i] = (m < a.M && k < a.K) ? __ldg(a.first ? a.Z + k + a.K * m : a.Z + m + a.M * k + a.M * a.K * b) : 0.f;
+        }
+      } else {
+        if (!warp_wait(&ffull[fslot], fph, fail)) {
+          if (lane == 0) atomicOr(fail, 1);
+          break;
+        }
+        const unsigned char* st = fring + (size_t)fslot * kF32Bytes;
+        if (a.first) {
+          // row r: 128 bytes under the 128-byte swizzle; this half is chunks 4 h .. 4 h + 3
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 v = *reinterpret_cast<const float4*>(st + sw128(r, 4 * h + j));
+            x[4 * j] = v.x; x[4 * j + 1] = v.y; x[4 * j + 2] = v.z; x[4 * j + 3] = v.w;
+          }
+        } else {
+          // box q holds rows k (128 bytes of l each); this lane's l is float `lane` of a row
+          const unsigned char* box = st + q * 4096 + (lane & 3) * 4;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int kk = 16 * h + i;
+            x[i] = *reinterpret_cast<const float*>(box + kk * 128 + (((lane >> 2) ^ (kk & 7)) << 4));
           }
         }
       }
-      // the CTA may not exit while a copy is still in flight
-      for (int j = (it > S ? it - S : 0); j < it; ++j)
-        if (!bar_wait(&fullb[j % S], (uint32_t)((j / S) & 1))) atomicOr(fail, 1);
-    }
-  } else if (warp <= kConvWarps) {
-    // ------------------------------------------------------------ split fp32 -> BF16 hi / lo
-    const int ct = t - 32;  // 0 .. 32 * kConvWarps - 1
-    int it = 0;
-    bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-      const int64_t b = tile / a.mtiles;
-      const int64_t m0 = (tile % a.mtiles) * BMT;
-      for (int kc = 0; kc < nk; ++kc, ++it) {
-        const int sf = SF > 0 ? it % SF : 0, sm = it % SM;
-        const int64_t k0 = (int64_t)kc * BKT;
-        float x[kUnitsPerThread][8];
-        if (a.direct) {
-          // issue the loads before waiting for the slot
-#pragma unroll
-          for (int j = 0; j < kUnitsPerThread; ++j) {
-            const int u = ct + 32 * kConvWarps * j;
-            if (a.first) {
-              const int r = ((u >> 5) << 3) + (u & 7), kq = (u >> 3) & 3;
-              const int64_t m = m0 + r;
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                const int64_t k = k0 + kq * 8 + i;
-                x[j][i] = (m < a.M && k < a.K) ? __ldg(a.Z + k + a.K * m) : 0.f;
-              }
-            } else {
-              const int r8 = (u >> 3) & 15;
-              const int64_t k = k0 + ((u >> 7) << 3) + (u & 7);
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                const int64_t m = m0 + r8 * 8 + i;
-                x[j][i] = (m < a.M && k < a.K) ? __ldg(a.Z + m + a.M * k + a.M * a.K * b) : 0.f;
-              }
-            }
-          }
-        } else {
-          if (failed(fail) || !bar_wait(&ffull[sf], (uint32_t)((it / SF) & 1))) {
-            atomicOr(fail, 1);
-            ok = false;
-            break;
-          }
-          const unsigned char* st = fring + (size_t)sf * kF32Bytes;
-#pragma unroll
-          for (int j = 0; j < kUnitsPerThread; ++j) {
-            const int u = ct + 32 * kConvWarps * j;
-            const unsigned char *p0, *p1;
-            if (a.first) {
-              const int r = (u >> 5) * 8 + (u & 7), kq = (u >> 3) & 3;
-              p0 = st + sw128(r, 2 * kq);
-              p1 = st + sw128(r, 2 * kq + 1);
-            } else {
-              const int r8 = (u >> 3) & 15, k = ((u >> 7) << 3) + (u & 7);
-              const unsigned char* sub = st + (r8 >> 2) * 4096;
-              p0 = sub + sw128(k, (r8 & 3) * 2);
-              p1 = sub + sw128(k, (r8 & 3) * 2 + 1);
-            }
-            const float4 v0 = *reinterpret_cast<const float4*>(p0);
-            const float4 v1 = *reinterpret_cast<const float4*>(p1);
-            x[j][0] = v0.x; x[j][1] = v0.y; x[j][2] = v0.z; x[j][3] = v0.w;
-            x[j][4] = v1.x; x[j][5] = v1.y; x[j][6] = v1.z; x[j][7] = v1.w;
-          }
-        }
-        // the operand slot is free once its R-hat chunk has landed (claimed by the producer)
-        if (failed(fail) || !bar_wait(&mfull[sm], (uint32_t)((it / SM) & 1))) {
-          atomicOr(fail, 1);
-          ok = false;
-          break;
-        }
-        unsigned char* hi = mring + (size_t)sm * mslot;
-        unsigned char* lo = hi + kAHalf;
-        uint4 h[kUnitsPerThread], l[kUnitsPerThread];
-#pragma unroll
-        for (int j = 0; j < kUnitsPerThread; ++j) split8(x[j], h[j], l[j]);
-        if (!a.direct) {
-          __syncwarp();
-          if (lane == 0) bar_arrive(&fempty[sf]);
-        }
-#pragma unroll
-        for (int j = 0; j < kUnitsPerThread; ++j) {
-          const int u = ct + 32 * kConvWarps * j;
-          uint32_t o;
-          if (a.first) {
-            // unit = (row r, 8 consecutive k): one 16-byte core-matrix row of the K-major tile
-            o = (uint32_t)(u >> 5) * a_sbo + (uint32_t)((u >> 3) & 3) * a_lbo + (uint32_t)(u & 7) * 16u;
-          } else {
-            // unit = (8 consecutive l, one k): one 16-byte core-matrix row of the MN-major tile
-            const int k = ((u >> 7) << 3) + (u & 7);
-            o = (uint32_t)((u >> 3) & 15) * a_sbo + (uint32_t)(k >> 3) * a_lbo + (uint32_t)(k & 7) * 16u;
-          }
-          *reinterpret_cast<uint4*>(hi + o) = h[j];
-          *reinterpret_cast<uint4*>(lo + o) = l[j];
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      uint32_t hi[8], lo[8];
+      split16(x, hi, lo);
+      if (!a.direct) {
         __syncwarp();
-        if (lane == 0) bar_arrive(&conv[sm]);
+        if (lane == 0) bar_arrive(&fempty[fslot]);
+      }
+      // the A stage pair is free once the MMAs of its previous K step have completed
+      if (it >= SB && !warp_wait(&kempty[pslot], pph ^ 1u, fail)) {
+        if (lane == 0) atomicOr(fail, 1);
+        break;
+      }
+      const int aslot = 2 * pslot + h;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t col = tmem + lanes + stage_col(aslot);
+      tmem_st8(col, hi);
+      tmem_st8(col + 8, lo);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) bar_arrive(&afull[aslot]);
+      // advance by kGroups half-steps
+      const int nit = (hs + kGroups) >> 1, dit = nit - it;
+      hs += kGroups;
+      it = nit;
+      kc += dit;
+      kq += dit;
+      while (kq >= nk) kq -= nk;
+      while (kc >= nk) {
+        kc -= nk;
+        tile += gridDim.x;
+      }
+      if (SF > 0) {
+        fslot += dit;
+        while (fslot >= SF) {
+          fslot -= SF;
+          fph ^= 1u;
+        }
+      }
+      pslot += dit;
+      while (pslot >= SB) {
+        pslot -= SB;
+        pph ^= 1u;
       }
     }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      // D F32, A and B BF16, A major per mode, B MN-major, N = Npad, M = 128
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((a.first ? 0u : 1u) << 15) | (1u << 16) |
-                             ((uint32_t)(a.Npad >> 3) << 17) | ((uint32_t)(BMT >> 4) << 24);
-      int it = 0, i = 0;
+      // D F32, A and B BF16, A K-major (rows in tensor-memory lanes), B MN-major, N = Npad,
+      // M = 128
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(a.Npad >> 3) << 17) |
+                             ((uint32_t)(BMT >> 4) << 24);
+      Ring rp(SB), rt(NA);
+      int i = 0;
       bool ok = true;
+      // a_ok / b_ok: the next A stage / R-hat chunk was seen complete by the test issued
+      // alongside the previous MMAs, so its blocking wait is skipped
+      bool a_ok = false, b_ok = false;
       for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++i) {
-        const int buf = i & 1;
-        if (i >= 2 && (failed(fail) || !bar_wait(&tempty[buf], (uint32_t)(((i >> 1) - 1) & 1)))) {
+        if (i >= NA && !bar_wait(&tempty[rt.slot], rt.phase ^ 1u, fail)) {
           atomicOr(fail, 1);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + (uint32_t)(buf * kTmemCols);
-        for (int kc = 0; kc < nk; ++kc, ++it) {
-          const int s = it % SM;
-          const uint32_t par = (uint32_t)((it / SM) & 1);
-          if (failed(fail) || !bar_wait(&conv[s], par) || !bar_wait(&mfull[s], par)) {
+        const uint32_t d = tmem + (uint32_t)(rt.slot * kAccStride);
+        for (int kc = 0; kc < nk && ok; ++kc) {
+          if (!b_ok && !bar_wait(&bfull[rp.slot], rp.phase, fail)) {
             atomicOr(fail, 1);
             ok = false;
             break;
           }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t ahi = su32(mring + (size_t)s * mslot), alo = ahi + kAHalf;
-          const uint32_t bhi = ahi + 2 * kAHalf, blo = bhi + a.bchunk;
-#pragma unroll
+          const uint32_t bhi = su32(bring + (size_t)rp.slot * bslot), blo = bhi + a.bchunk;
+          Ring np = rp;
+          np.next();
           for (int kk = 0; kk < BKT / 16; ++kk) {
-            const uint32_t ao = kk * 2 * a_lbo, bo = kk * 2 * b_lbo;
-            const uint64_t dAh = sdesc(ahi + ao, a_lbo, a_sbo), dAl = sdesc(alo + ao, a_lbo, a_sbo);
+            const int as = 2 * rp.slot + kk;
+            if (!a_ok && !bar_wait(&afull[as], rp.phase, fail)) {
+              atomicOr(fail, 1);
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ahi = tmem + stage_col(as), alo = ahi + 8;
+            const uint32_t bo = kk * 2 * b_lbo;
             const uint64_t dBh = sdesc(bhi + bo, b_lbo, b_sbo), dBl = sdesc(blo + bo, b_lbo, b_sbo);
-            mma_bf16(d, dAh, dBh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-            mma_bf16(d, dAh, dBl, idesc, 1u);
-            mma_bf16(d, dAl, dBh, idesc, 1u);
+            // test the next half-step's A stage and, at the end of the K step, the next chunk
+            const bool last = kk == BKT / 16 - 1;
+            const uint64_t* ta = last ? &afull[2 * np.slot] : &afull[as + 1];
+            const uint32_t pa = last ? np.phase : rp.phase;
+            const uint32_t seen = mma3_test(d, ahi, alo, dBh, dBl, idesc, (kc > 0 || kk > 0) ? 1u : 0u, ta, pa,
+                                            &bfull[np.slot], np.phase);
+            a_ok = (seen & 1u) != 0;
+            if (last) b_ok = (seen & 2u) != 0;
           }
-          // the slot may be refilled once these MMAs have read it
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           su32(&mempty[s]))
-                       : "memory");
+          // the K step's R-hat slot and A stage pair may be refilled once these MMAs have read them
+          if (ok) mma_commit(&kempty[rp.slot]);
+          rp = np;
         }
-        // accumulator `buf` is complete once every MMA issued so far has finished
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         su32(&tfull[buf]))
-                     : "memory");
+        // accumulator `rt.slot` is complete once every MMA issued so far has finished
+        if (ok) mma_commit(&tfull[rt.slot]);
+        rt.next();
       }
+      // tensor memory is released only after every MMA issued has completed
+      mma_commit(mdone);
+      if (!bar_wait(mdone, 0, nullptr)) atomicOr(fail, 1);
     }
   } else {
     // ------------------------------------------------------------ epilogue (4 warps): TMEM -> Y
     const int quarter = warp & 3;  // a warp reaches TMEM lanes 32 * (warp id mod 4) .. + 31
-    int i = 0;
-    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++i) {
-      const int buf = i & 1;
-      bool ok = !failed(fail) && bar_wait(&tfull[buf], (uint32_t)((i >> 1) & 1));
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) {
+    Ring rt(NA);
+    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+      if (!warp_wait(&tfull[rt.slot], rt.phase, fail)) {
         if (lane == 0) atomicOr(fail, 1);
         break;
       }
@@ -406,7 +516,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
       const int64_t b = tile / a.mtiles;
       const int64_t row = (tile % a.mtiles) * BMT + 32 * quarter + lane;
       float* y = a.Y + b * a.ldy_b + row * a.ldy_m;
-      const uint32_t base = tmem + (uint32_t)(buf * kTmemCols) + ((uint32_t)(32 * quarter) << 16);
+      const uint32_t base = tmem + (uint32_t)(rt.slot * kAccStride) + ((uint32_t)(32 * quarter) << 16);
       for (int c0 = 0; c0 < a.Npad; c0 += 16) {
         uint32_t v[16];
         asm volatile(
@@ -432,13 +542,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) bar_arrive(&tempty[buf]);
+      if (lane == 0) bar_arrive(&tempty[rt.slot]);
+      rt.next();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == kMmaWarp)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   if (t == 0 && *fail && a.err) atomicOr(a.err, 1);
 }
 
@@ -593,25 +704,50 @@ int ttm_mode_tc(const Shape& s, const float* Z, int mode, const double* Rh, int6
     }
     a.direct = r == CUDA_SUCCESS ? 0 : 1;
   }
+  // R-hat chunks: a 2-D tensor map over the split buffer seen as rows of 64 BF16 (128 bytes),
+  // Npad rows per chunk (bulk copies if it cannot be encoded)
+  CUtensorMap bmap;
+  std::memset(&bmap, 0, sizeof(bmap));
+  a.btm = 0;
+  if (encode_fn() != nullptr) {
+    cuuint64_t dims[2] = {64, (cuuint64_t)nk * Npad};
+    cuuint64_t strides[1] = {128};
+    cuuint32_t box[2] = {64, (cuuint32_t)Npad};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode_fn()(&bmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, bsplit, dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    a.btm = r == CUDA_SUCCESS ? 1 : 0;
+  }
   a.mtiles = cdiv(a.M, BMT);
   a.ntiles = a.mtiles * a.batch;
   a.vec4 = mode == 0 && (Ic % 4) == 0 && (reinterpret_cast<uintptr_t>(Y) % 16) == 0;
   const int64_t grid = std::min<int64_t>(a.ntiles, num_sms());
-  // operand ring: 3 slots (4 when they are small); fp32 ring: the rest of shared memory, 2..8
-  const size_t mslot = 2 * kAHalf + 2 * (size_t)bchunk;
+  // tensor memory: accumulators at columns 0 and 256 when that leaves room for three K16 A
+  // stages after each (Npad <= 208), else one accumulator at 0; A stages follow each
+  // accumulator, an even number of them (pairs per K step), up to eight.  The parity waits need
+  // at least kGroups A stages: a splitter group then never tests a barrier more than one phase
+  // ahead (its own wait kGroups half-steps earlier covered the phase before).
+  a.nacc = (kAccStride - Npad) / kAStageCols >= 3 ? 2 : 1;
+  a.n0 = (a.nacc == 2 ? kAccStride - Npad : kTmemCols - Npad) / kAStageCols;
+  a.sa = std::min(kMaxAStages, a.nacc == 2 ? 2 * a.n0 : a.n0) & ~1;
+  // shared memory: one R-hat slot per A stage pair (a K step frees both with one commit), then
+  // an even fp32 ring of 2..8 slots (each splitter group then consumed the previous use of a
+  // slot itself)
+  const size_t bslot = 2 * (size_t)bchunk;
   const size_t cap = (size_t)smem_optin_tc();
-  a.sm = mslot <= 32768 ? 4 : 3;
-  if (kStageBase + a.sm * mslot + (a.direct ? 0 : 2 * kF32Bytes) > cap) a.sm = 2;
-  a.sf = a.direct ? 0 : (int)std::min<size_t>(8, (cap - kStageBase - a.sm * mslot) / kF32Bytes);
-  if (!a.direct && a.sf < 2) return CPMG_UNSUPPORTED;
+  a.sb = a.sa / 2;
+  if (kStageBase + a.sb * bslot > cap) return CPMG_UNSUPPORTED;
+  a.sf = a.direct ? 0 : (int)std::min<size_t>(kMaxRing, (cap - kStageBase - a.sb * bslot) / kF32Bytes) & ~1;
+  if (a.sa < kGroups || a.sb < 2 || (!a.direct && a.sf < 2)) return CPMG_UNSUPPORTED;
   // more than half of an SM's shared memory: one CTA per SM, so the 512-column tensor-memory
   // allocation never waits for another CTA
   const size_t smem =
-      std::min(cap, std::max<size_t>(kStageBase + a.sm * mslot + (size_t)a.sf * kF32Bytes, 120 * 1024));
+      std::min(cap, std::max<size_t>(kStageBase + a.sb * bslot + (size_t)a.sf * kF32Bytes, 120 * 1024));
   cudaFuncSetAttribute(k_ttm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
   const unsigned evflags = ev_external ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (ev0) CPMG_CUDA_TRY(cudaEventRecordWithFlags(ev0, st, evflags));
-  k_ttm_tc<<<(unsigned)grid, THREADS, smem, st>>>(tmap, a);
+  k_ttm_tc<<<(unsigned)grid, THREADS, smem, st>>>(tmap, bmap, a);
   CPMG_CUDA_TRY(cudaGetLastError());
   if (ev1) CPMG_CUDA_TRY(cudaEventRecordWithFlags(ev1, st, evflags));
   return CPMG_OK;
