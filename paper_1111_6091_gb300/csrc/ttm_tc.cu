@@ -171,6 +171,15 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
                : "memory");
 }
 
+// sixteen 32-bit columns of this warp's 32 tensor-memory lanes (completion: tcgen05.wait::ld)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
 // x -> (hi, lo) for 16 floats; column j packs elements 2j (low half) and 2j + 1 (high half),
 // the order of consecutive K elements in memory.  Two floats per conversion instruction; a
 // BF16 value widens to float exactly by a 16-bit shift.
@@ -195,6 +204,7 @@ struct TcArgs {
   int first;            // 1: mode 1 (rows of A are g, k contiguous), 0: later mode (rows are l)
   int direct;           // 1: splitters load Z from global memory (no tensor map)
   int btm;              // 1: R-hat chunks through their tensor map (rows of 128 bytes), else bulk copies
+  int ytm;              // 1: mode-1 output tiles through TMA stores (Y rows of Ic floats)
   int sf, sb, sa;       // slots of the fp32 ring, of the R-hat ring, K16 A stages in tensor memory
   int nacc;             // accumulators in tensor memory: 1 (at column 0) or 2 (at 0 and 256)
   int n0;               // A stages after the first accumulator; the rest follow the second
@@ -218,7 +228,8 @@ struct TcArgs {
 // in shared memory and A stages in tensor memory (both freed by the MMA commit).  With two
 // accumulators the epilogue of one tile overlaps the main loop of the next.
 __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ CUtensorMap tmap,
-                                                        const __grid_constant__ CUtensorMap bmap, TcArgs a) {
+                                                        const __grid_constant__ CUtensorMap bmap,
+                                                        const __grid_constant__ CUtensorMap ymap, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int SF = a.sf, SB = a.sb, SA = a.sa, NA = a.nacc;
@@ -239,6 +250,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
   int* fail = reinterpret_cast<int*>(smem + 520);
   unsigned char* fring = smem + kStageBase;
   unsigned char* bring = fring + (size_t)SF * kF32Bytes;
+  // TMA-store staging: per epilogue warp two 4 KB buffers (32 rows x 128 bytes, 128-byte swizzle)
+  unsigned char* ystage = smem + (((uint32_t)(bring - smem) + (uint32_t)SB * 2u * a.bchunk + 1023u) & ~1023u);
   const uint32_t bslot = 2 * a.bchunk;
   const int nk = (int)((a.K + BKT - 1) / BKT);
   // CTAs start their K loops at different chunks, so that the SMs do not all read the same
@@ -507,6 +520,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
     // ------------------------------------------------------------ epilogue (4 warps): TMEM -> Y
     const int quarter = warp & 3;  // a warp reaches TMEM lanes 32 * (warp id mod 4) .. + 31
     Ring rt(NA);
+    unsigned char* stg = ystage + quarter * 8192;
+    int nst = 0;  // TMA stores this warp has issued (their buffer alternates)
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
       if (!warp_wait(&tfull[rt.slot], rt.phase, fail)) {
         if (lane == 0) atomicOr(fail, 1);
@@ -514,29 +529,58 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int64_t b = tile / a.mtiles;
-      const int64_t row = (tile % a.mtiles) * BMT + 32 * quarter + lane;
-      float* y = a.Y + b * a.ldy_b + row * a.ldy_m;
+      const int64_t row0 = (tile % a.mtiles) * BMT + 32 * quarter;
+      const int64_t row = row0 + lane;
       const uint32_t base = tmem + (uint32_t)(rt.slot * kAccStride) + ((uint32_t)(32 * quarter) << 16);
-      for (int c0 = 0; c0 < a.Npad; c0 += 16) {
-        uint32_t v[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(base + (uint32_t)c0));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < a.M) {
-          if (a.vec4) {
-#pragma unroll
-            for (int j = 0; j < 16; j += 4)
-              if (c0 + j < a.Ic)
-                *reinterpret_cast<float4*>(y + c0 + j) =
-                    make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
-                                __uint_as_float(v[j + 3]));
+      if (a.ytm) {
+        // 32 columns at a time: TMEM -> registers -> swizzled staging -> one TMA store of a
+        // 32 x 32 box (rows past M and columns past Ic are clipped by the copy)
+        for (int c0 = 0; c0 < a.Npad; c0 += 32, ++nst) {
+          uint32_t v[32];
+          tmem_ld16(base + (uint32_t)c0, v);
+          if (c0 + 16 < a.Npad) {
+            tmem_ld16(base + (uint32_t)(c0 + 16), v + 16);
           } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (c0 + j < a.Ic) y[(int64_t)(c0 + j) * a.ldy_c] = __uint_as_float(v[j]);
+            for (int j = 16; j < 32; ++j) v[j] = 0u;
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          unsigned char* buf = stg + (nst & 1) * 4096;
+          // the buffer's previous store (two stores ago) must have read it
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<uint4*>(buf + sw128(lane, j)) = make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            asm volatile(
+                "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(&ymap), "r"(c0),
+                "r"((int)row0), "r"(su32(buf))
+                : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+        }
+      } else {
+        float* y = a.Y + b * a.ldy_b + row * a.ldy_m;
+        for (int c0 = 0; c0 < a.Npad; c0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(base + (uint32_t)c0, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (row < a.M) {
+            if (a.vec4) {
+#pragma unroll
+              for (int j = 0; j < 16; j += 4)
+                if (c0 + j < a.Ic)
+                  *reinterpret_cast<float4*>(y + c0 + j) =
+                      make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                                  __uint_as_float(v[j + 3]));
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (c0 + j < a.Ic) y[(int64_t)(c0 + j) * a.ldy_c] = __uint_as_float(v[j]);
+            }
           }
         }
       }
@@ -545,6 +589,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
       if (lane == 0) bar_arrive(&tempty[rt.slot]);
       rt.next();
     }
+    // the CTA may not exit (and its shared memory be reused) before its stores have read it
+    if (a.ytm && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -719,6 +765,20 @@ int ttm_mode_tc(const Shape& s, const float* Z, int mode, const double* Rh, int6
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     a.btm = r == CUDA_SUCCESS ? 1 : 0;
   }
+  // mode-1 output through TMA stores: a 2-D map over Y (Ic floats per row), 32 x 32 boxes
+  CUtensorMap ymap;
+  std::memset(&ymap, 0, sizeof(ymap));
+  a.ytm = 0;
+  if (mode == 0 && (Ic % 4) == 0 && Ic >= 32 && (reinterpret_cast<uintptr_t>(Y) % 16) == 0 && encode_fn() != nullptr) {
+    cuuint64_t dims[2] = {(cuuint64_t)Ic, (cuuint64_t)G};
+    cuuint64_t strides[1] = {(cuuint64_t)Ic * 4};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode_fn()(&ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Y, dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    a.ytm = r == CUDA_SUCCESS ? 1 : 0;
+  }
   a.mtiles = cdiv(a.M, BMT);
   a.ntiles = a.mtiles * a.batch;
   a.vec4 = mode == 0 && (Ic % 4) == 0 && (reinterpret_cast<uintptr_t>(Y) % 16) == 0;
@@ -737,17 +797,20 @@ int ttm_mode_tc(const Shape& s, const float* Z, int mode, const double* Rh, int6
   const size_t bslot = 2 * (size_t)bchunk;
   const size_t cap = (size_t)smem_optin_tc();
   a.sb = a.sa / 2;
-  if (kStageBase + a.sb * bslot > cap) return CPMG_UNSUPPORTED;
-  a.sf = a.direct ? 0 : (int)std::min<size_t>(kMaxRing, (cap - kStageBase - a.sb * bslot) / kF32Bytes) & ~1;
+  // TMA-store staging (4 warps x 2 x 4 KB, 1 KB aligned) after the R-hat ring
+  const size_t ybytes = a.ytm ? 4 * 2 * 4096 + 1024 : 0;
+  if (kStageBase + a.sb * bslot + ybytes > cap) return CPMG_UNSUPPORTED;
+  a.sf = a.direct ? 0
+                  : (int)std::min<size_t>(kMaxRing, (cap - kStageBase - a.sb * bslot - ybytes) / kF32Bytes) & ~1;
   if (a.sa < kGroups || a.sb < 2 || (!a.direct && a.sf < 2)) return CPMG_UNSUPPORTED;
   // more than half of an SM's shared memory: one CTA per SM, so the 512-column tensor-memory
   // allocation never waits for another CTA
   const size_t smem =
-      std::min(cap, std::max<size_t>(kStageBase + a.sb * bslot + (size_t)a.sf * kF32Bytes, 120 * 1024));
+      std::min(cap, std::max<size_t>(kStageBase + a.sb * bslot + (size_t)a.sf * kF32Bytes + ybytes, 120 * 1024));
   cudaFuncSetAttribute(k_ttm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
   const unsigned evflags = ev_external ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (ev0) CPMG_CUDA_TRY(cudaEventRecordWithFlags(ev0, st, evflags));
-  k_ttm_tc<<<(unsigned)grid, THREADS, smem, st>>>(tmap, bmap, a);
+  k_ttm_tc<<<(unsigned)grid, THREADS, smem, st>>>(tmap, bmap, ymap, a);
   CPMG_CUDA_TRY(cudaGetLastError());
   if (ev1) CPMG_CUDA_TRY(cudaEventRecordWithFlags(ev1, st, evflags));
   return CPMG_OK;
