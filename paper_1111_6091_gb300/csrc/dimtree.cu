@@ -213,13 +213,17 @@ __global__ void __launch_bounds__(kWThreads) k_dt_w(const TZ* __restrict__ X, in
       for (int v = 0; v < VW; ++v) W[p0 + v + P * r] = Acc::out(acc[v][r]);
 }
 
-template <typename TZ, int PREC, int VW>
+// RPMAX: the largest padded rank instantiated (8 for the float-pair two-row kernel, which is
+// only launched up to R = 8: its wider instantiations would spill)
+template <typename TZ, int PREC, int VW, int RPMAX = 16>
 static void launch_w_rp(const TZ* X, int64_t P, int64_t K, int R, const double* C, double* W, cudaStream_t st) {
   const unsigned grid = (unsigned)((P / VW + kWThreads - 1) / kWThreads);
   if (R <= 4) k_dt_w<TZ, PREC, VW, 4><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
-  else if (R <= 8) k_dt_w<TZ, PREC, VW, 8><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
-  else if (R <= 12) k_dt_w<TZ, PREC, VW, 12><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
-  else k_dt_w<TZ, PREC, VW, 16><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
+  else if (R <= 8 || RPMAX <= 8) k_dt_w<TZ, PREC, VW, 8><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
+  else if constexpr (RPMAX > 8) {
+    if (R <= 12) k_dt_w<TZ, PREC, VW, 12><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
+    else k_dt_w<TZ, PREC, VW, 16><<<grid, kWThreads, 0, st>>>(X, P, K, R, C, W);
+  }
 }
 
 int launch_dt_w(const void* X, int zdtype, int64_t P, int64_t K, int R, const double* C, int prec, double* W,
@@ -249,7 +253,7 @@ int launch_dt_w(const void* X, int zdtype, int64_t P, int64_t K, int R, const do
                           : launch_w_rp<float, P_FP32, 1>(x, P, K, R, C, W, st);
         break;
       case P_DF:  // two rows of float-pair accumulators fit the registers up to R = 8
-        (vw >= 2 && R <= 8) ? launch_w_rp<float, P_DF, 2>(x, P, K, R, C, W, st)
+        (vw >= 2 && R <= 8) ? launch_w_rp<float, P_DF, 2, 8>(x, P, K, R, C, W, st)
                             : launch_w_rp<float, P_DF, 1>(x, P, K, R, C, W, st);
         break;
       default:

@@ -137,28 +137,33 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// One K16 half-step of split BF16: D [+]= A_hi B_hi + A_hi B_lo + A_lo B_hi, A in tensor memory,
-// B in shared memory.  The same instruction block tests (without blocking) whether phase p0 of
-// barrier b0 and phase p1 of b1 have completed, so that the latency of those tests overlaps
-// the issue of the three MMAs; bit 0 / bit 1 of the result report them.
-__device__ __forceinline__ uint32_t mma3_test(uint32_t d, uint32_t ahi, uint32_t alo, uint64_t dBh, uint64_t dBl,
-                                              uint32_t idesc, uint32_t acc, const uint64_t* b0, uint32_t p0,
-                                              const uint64_t* b1, uint32_t p1) {
+// One 32-wide K step of split BF16 (two K16 half-steps, six MMAs), then a commit that arrives
+// on `done` once they have completed.  The block first tests (without blocking) phase p0 of
+// barrier b0 and phase p1 of b1, so that the latency of the tests overlaps the MMA issue; bit 0
+// / bit 1 of the result report them.
+__device__ __forceinline__ uint32_t mma6_commit_test(uint32_t d, uint32_t a0h, uint32_t a0l, uint32_t a1h, uint32_t a1l,
+                                                     uint64_t b0h, uint64_t b0l, uint64_t b1h, uint64_t b1l,
+                                                     uint32_t idesc, uint32_t acc, const uint64_t* done,
+                                                     const uint64_t* t0, uint32_t p0, const uint64_t* t1, uint32_t p1) {
   uint32_t r0, r1;
   asm volatile(
       "{\n\t.reg .pred pa, pt, q0, q1;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 q0, [%9], %10;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 q1, [%11], %12;\n\t"
-      "setp.ne.b32 pa, %8, 0;\n\t"
-      "setp.eq.b32 pt, %8, %8;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%3], %5, %7, pa;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%3], %6, %7, pt;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%4], %5, %7, pt;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q0, [%14], %15;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q1, [%16], %17;\n\t"
+      "setp.ne.b32 pa, %12, 0;\n\t"
+      "setp.eq.b32 pt, %12, %12;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%3], %7, %11, pa;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%3], %8, %11, pt;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%4], %7, %11, pt;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%5], %9, %11, pt;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%5], %10, %11, pt;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%2], [%6], %9, %11, pt;\n\t"
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%13];\n\t"
       "selp.u32 %0, 1, 0, q0;\n\t"
       "selp.u32 %1, 1, 0, q1;\n\t}"
       : "=r"(r0), "=r"(r1)
-      : "r"(d), "r"(ahi), "r"(alo), "l"(dBh), "l"(dBl), "r"(idesc), "r"(acc), "r"(su32(b0)), "r"(p0),
-        "r"(su32(b1)), "r"(p1)
+      : "r"(d), "r"(a0h), "r"(a0l), "r"(a1h), "r"(a1l), "l"(b0h), "l"(b0l), "l"(b1h), "l"(b1l), "r"(idesc),
+        "r"(acc), "r"(su32(done)), "r"(su32(t0)), "r"(p0), "r"(su32(t1)), "r"(p1)
       : "memory");
   return r0 | (r1 << 1);
 }
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
                                                         const __grid_constant__ CUtensorMap ymap, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int SF = a.sf, SB = a.sb, SA = a.sa, NA = a.nacc;
+  const int SF = a.sf, SB = a.sb, NA = a.nacc;  // A stages: 2 SB (a pair per K step)
   // first tensor-memory column of K16 A stage s: the columns after each accumulator
   auto stage_col = [&](int s) -> uint32_t {
     return (uint32_t)(s < a.n0 ? a.Npad + kAStageCols * s : kAccStride + a.Npad + kAStageCols * (s - a.n0));
@@ -266,7 +271,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
       bar_init(&bfull[s], 1);
       bar_init(&kempty[s], 1);
     }
-    for (int s = 0; s < kMaxAStages; ++s) bar_init(&afull[s], 4);
+    for (int s = 0; s < kMaxAStages; ++s) bar_init(&afull[s], 8);  // both half-steps, four warps each
     for (int j = 0; j < 2; ++j) {
       bar_init(&tfull[j], 1);
       bar_init(&tempty[j], 4);
@@ -430,7 +435,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) bar_arrive(&afull[aslot]);
+      if (lane == 0) bar_arrive(&afull[pslot]);
       // advance by kGroups half-steps
       const int nit = (hs + kGroups) >> 1, dit = nit - it;
       hs += kGroups;
@@ -463,6 +468,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(a.Npad >> 3) << 17) |
                              ((uint32_t)(BMT >> 4) << 24);
       Ring rp(SB), rt(NA);
+      const uint64_t dB0 = sdesc(su32(bring), b_lbo, b_sbo);
       int i = 0;
       bool ok = true;
       // a_ok / b_ok: the next A stage / R-hat chunk was seen complete by the test issued
@@ -481,31 +487,27 @@ __global__ void __launch_bounds__(THREADS, 1) k_ttm_tc(const __grid_constant__ C
             ok = false;
             break;
           }
-          const uint32_t bhi = su32(bring + (size_t)rp.slot * bslot), blo = bhi + a.bchunk;
+          // a descriptor's start-address field is the shared-memory address / 16 (below 2^18
+          // bytes, so the field never carries): slot, half-step and hi / lo are added offsets
+          const uint64_t dBh = dB0 + ((uint32_t)rp.slot * bslot >> 4), dBl = dBh + (a.bchunk >> 4);
           Ring np = rp;
           np.next();
-          for (int kk = 0; kk < BKT / 16; ++kk) {
-            const int as = 2 * rp.slot + kk;
-            if (!a_ok && !bar_wait(&afull[as], rp.phase, fail)) {
-              atomicOr(fail, 1);
-              ok = false;
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ahi = tmem + stage_col(as), alo = ahi + 8;
-            const uint32_t bo = kk * 2 * b_lbo;
-            const uint64_t dBh = sdesc(bhi + bo, b_lbo, b_sbo), dBl = sdesc(blo + bo, b_lbo, b_sbo);
-            // test the next half-step's A stage and, at the end of the K step, the next chunk
-            const bool last = kk == BKT / 16 - 1;
-            const uint64_t* ta = last ? &afull[2 * np.slot] : &afull[as + 1];
-            const uint32_t pa = last ? np.phase : rp.phase;
-            const uint32_t seen = mma3_test(d, ahi, alo, dBh, dBl, idesc, (kc > 0 || kk > 0) ? 1u : 0u, ta, pa,
-                                            &bfull[np.slot], np.phase);
-            a_ok = (seen & 1u) != 0;
-            if (last) b_ok = (seen & 2u) != 0;
+          if (!a_ok && !bar_wait(&afull[rp.slot], rp.phase, fail)) {
+            atomicOr(fail, 1);
+            ok = false;
+            break;
           }
-          // the K step's R-hat slot and A stage pair may be refilled once these MMAs have read them
-          if (ok) mma_commit(&kempty[rp.slot]);
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // both half-steps, the commit that frees the K step's R-hat slot and A stage pair, and
+          // tests of the next K step's A stage pair and R-hat chunk
+          static_assert(BKT == 32, "one K step is two K16 half-steps");
+          const uint32_t a0 = tmem + stage_col(2 * rp.slot), a1 = tmem + stage_col(2 * rp.slot + 1);
+          const uint64_t bo = (2 * b_lbo) >> 4;
+          const uint32_t seen = mma6_commit_test(d, a0, a0 + 8, a1, a1 + 8, dBh, dBl, dBh + bo, dBl + bo, idesc,
+                                                 kc > 0 ? 1u : 0u, &kempty[rp.slot], &afull[np.slot], np.phase,
+                                                 &bfull[np.slot], np.phase);
+          a_ok = (seen & 1u) != 0;
+          b_ok = (seen & 2u) != 0;
           rp = np;
         }
         // accumulator `rt.slot` is complete once every MMA issued so far has finished
