@@ -383,7 +383,7 @@ def run_gpu(args):
         extra["multilevel_100cubed"] = run_multilevel_100cubed(ctx, stream, parity=rank == 0 and not args.no_cpu_baseline)
         extra.update(run_400cubed(ctx, stream, hbm, how))
         if args.serve_requests > 0:
-            extra["served"] = run_served(args.serve_requests)
+            extra["served"] = run_served(args.serve_requests, parity=rank == 0 and not args.no_cpu_baseline)
         if not args.no_paper_dense:
             extra["paper_dense_ijk"] = run_paper_dense(ctx, stream)
             extra["paper_laplacian"] = run_paper_laplacian(ctx, stream)
@@ -691,11 +691,18 @@ def run_paper_laplacian(ctx, stream):
             "tests": out, "note": "paper: MATLAB on a 2.5 GHz Core 2 Duo, sparse tensors, averages of 10 starts; context only"}
 
 
-def run_served(nreq, pool_small=96, pool_large=4, seed=12345, precisions=("mixed", "fp64"), large_multilevel=False):
-    """Poisson arrivals (2000 requests/s) of CP-ALS requests to g < 1e-8 (at most 1000 sweeps):
+def run_served(nreq, pool_small=96, pool_large=4, seed=12345, precisions=("mixed", "fp64"), large_multilevel=False,
+               parity=False):
+    """Poisson arrivals (2000 requests/s) of CP-ALS requests to g < 1e-8 (at most 1e4 sweeps):
     95% drawn from a pool of tensors of the batch workload, 5% 256^3 R=8 tensors; admission
     budget 120 GB.  Served with MIXED and with plain FP64 arithmetic; p50/p99 latency and
-    throughput of each."""
+    throughput of each.
+
+    parity (the oracle leg): for the MIXED arm, the served results of a 1 % sample of the small
+    requests against the oracle's ALS from the same start with the same stopping test (factor
+    error, relative f), and for every large tensor served the oracle's own FP64 g (Eq. gradConv)
+    and f of the served factors (an oracle solve of a 256^3 tensor takes far longer than the run;
+    requests for the same tensor and start give bitwise the same factors)."""
     import torch
     from paper_1111_6091_gb300 import cpmg, synth
     small = batch_problems(pool_small, seed=1)
@@ -744,12 +751,15 @@ def run_served(nreq, pool_small=96, pool_large=4, seed=12345, precisions=("mixed
             tickets.append(submit(key, As[i]))
         srv.wait(900.0)
         dt = time.perf_counter() - t0
-        lats, conv = [], 0
+        lats, conv, results = [], 0, []
         for t in tickets:
             r = srv.poll(t)
+            results.append(r)
             lats.append(r["seconds"])
             conv += r["status"] == cpmg.OK
         lat_l = [l for l, key in zip(lats, picks) if key[0] == "L"]
+        if parity and name == "mixed":
+            out["err_vs_oracle"] = served_parity(results, picks, small, large, As, nreq)
         lats = np.sort(np.array(lats))
         out[name] = {"p50_s": float(np.percentile(lats, 50)), "p99_s": float(np.percentile(lats, 99)),
                      "req_per_s": nreq / dt, "seconds": dt, "converged": conv,
@@ -757,6 +767,43 @@ def run_served(nreq, pool_small=96, pool_large=4, seed=12345, precisions=("mixed
                      "large_requests": len(lat_l)}
         ctx.close()
     return out
+
+
+def served_parity(results, picks, small, large, As, nreq):
+    """Served results (the polled result dicts, in request order) against the oracle (see
+    run_served)."""
+    from paper_1111_6091_gb300 import cpmg
+    from oracle import align, tensor as T
+    step = max(1, nreq // max(1, nreq // 100))
+    rows, seen = [], set()
+    for i in range(0, nreq, step):
+        key = picks[i]
+        if key[0] != "S" or key in seen:
+            continue
+        seen.add(key)
+        r = results[i]
+        _, Ao, ito, go = oracle_batch_tensor(small[key[1]])
+        got = [cpmg.to_numpy(a) for a in As[i]]
+        Z64 = small[key[1]].Z.astype(np.float64)
+        fo, fg = T.f_value(Z64, Ao), T.f_value(Z64, got)
+        rows.append({"request": i, "pool_tensor": key[1], "factor_err": align.factor_error(Ao, got),
+                     "rel_f": abs(fg - fo) / fo, "sweeps_gpu": r["iters_als"], "sweeps_oracle": ito})
+    large_rows = []
+    for k in range(len(large)):
+        idx = [i for i, key in enumerate(picks) if key == ("L", k)]
+        if not idx:
+            continue
+        i = idx[0]
+        r = results[i]
+        got = [cpmg.to_numpy(a) for a in As[i]]
+        Z64 = large[k].Z.astype(np.float64)
+        g_o, f_o = T.g_value(Z64, got), T.f_value(Z64, got)
+        same = all(all(np.array_equal(cpmg.to_numpy(a), b) for a, b in zip(As[j], got)) for j in idx[1:])
+        large_rows.append({"pool_tensor": k, "requests": len(idx), "g_oracle": g_o, "g_reported": r["g"],
+                           "rel_f_reported_vs_oracle": abs(r["f"] - f_o) / f_o, "all_requests_bitwise_equal": same})
+    return {"small_sample": f"{len(rows)} requests (every {step}th, one per pool tensor)",
+            "max_factor_err": max((x["factor_err"] for x in rows), default=None),
+            "max_rel_f": max((x["rel_f"] for x in rows), default=None), "small": rows, "large": large_rows}
 
 
 def run_ttm_case(args):
@@ -878,7 +925,8 @@ def main():
         ctx.close()
     elif args.served_only:
         print(json.dumps({"served": run_served(args.serve_requests, precisions=tuple(args.serve_precisions.split(",")),
-                                               large_multilevel=args.serve_large_multilevel)}), flush=True)
+                                               large_multilevel=args.serve_large_multilevel,
+                                               parity=not args.no_cpu_baseline)}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
