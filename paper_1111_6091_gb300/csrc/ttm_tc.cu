@@ -10,21 +10,26 @@
 // products hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor memory; the dropped lo*lo
 // term and the rounding of lo leave a relative error near 2^-16 per product.
 //
-// The A operand lives in tensor memory.  Splitter threads own one row of the 128-row tile each
-// (its tensor-memory lane), split its 16 k values of a half stage and write hi and lo with
-// tcgen05.st; the MMA reads A from there and only B from shared memory.  Shared memory carries
-// the fp32 tiles of Z (written by TMA, read once by the splitters) and a ring of pre-split
-// R-hat chunks, so per 32-wide K step it moves about 16 + 16 + 26 + 40 KB (Ic = 200) instead of
-// also writing the split A tile and reading it three times.
+// The A operand lives in tensor memory. Splitter threads own one row of the 128-row tile each
+// (its tensor-memory lane). A thread splits the 16 k values of a half-step and writes hi and lo
+// with tcgen05.st. The MMA reads A from there and only B from shared memory. Shared memory carries
+// the fp32 tiles of Z, written by TMA and read once by the splitters, and a ring of pre-split R-hat
+// chunks.
 //
-// Persistent CTAs of 480 threads, one per SM, walk 128-row output tiles:
+// Persistent CTAs of 736 threads, one per SM, walk 128-row output tiles:
 //   warp 0      producer: fp32 tiles of Z by cp.async.bulk.tensor (128-byte swizzle)
-//   warp 1      producer: pre-split R-hat chunks by cp.async.bulk, in a ring of their own
-//   warp 2      allocates tensor memory; one lane issues tcgen05.mma (A from tensor memory)
-//   warps 3-10  splitters: two per lane quarter, one per half of the 32-wide K step (or
-//               loading Z straight from global memory when its strides do not suit a tensor map)
-//   warps 11-14 drain an accumulator into Y while the next tile is computed (two accumulators
-//               when they leave room for four A stages, else one)
+//   warp 1      producer: pre-split R-hat chunks through a 2-D tensor map (bulk copies if that
+//               cannot be encoded), one slot per K step in flight
+//   warp 2      allocates tensor memory. One lane issues a K step at a time: six tcgen05.mma
+//               (hi*hi + hi*lo + lo*hi for two K16 halves, A from tensor memory), then one commit
+//               that frees the step's R-hat slot and A stage pair. The same instruction block
+//               tests the next step's barriers without blocking, so those waits overlap the MMAs.
+//   warps 3-18  splitters: four groups of four warps (one per lane quarter) take the K16
+//               half-steps in turn, so four are in flight at once. When Z's strides do not
+//               suit a tensor map, they load Z straight from global memory.
+//   warps 19-22 drain an accumulator while the next tile is computed. There are two
+//               accumulators, at columns 0 and 256, when Ic <= 208, else one. Mode-1 tiles
+//               leave through TMA stores from a swizzled staging buffer.
 // Every mbarrier wait gives up after about 2 s, records an error and lets the CTA unwind.
 #include <cuda.h>
 #include <cuda_bf16.h>
