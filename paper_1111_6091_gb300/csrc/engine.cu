@@ -284,8 +284,10 @@ static int prof_ttm(cpmg_ctx* c, const Shape& s, int dtype, const double* const*
   for (int k = 0; k < 2 * kMaxModes; ++k) ev[k] = nullptr;
   if (!c->profile || !tensor_cores || dtype != CPMG_F32) return CPMG_OK;
   Shape cur = s;
-  for (int n = 0; n < s.N; ++n) {
-    if (!Rh[n]) continue;
+  int order[kMaxModes];
+  const int k = ttm_order(s, dtype, Rh, Ic, tensor_cores, order);
+  for (int j = 0; j < k; ++j) {
+    const int n = order[j];
     const double in = 4.0 * (double)cur.numel();
     const bool tc = ttm_tc_supported(cur, dtype, n, Ic[n]);
     cur.dims[n] = Ic[n];

@@ -149,13 +149,28 @@ size_t ttm_max_intermediate(const Shape& s, int dtype, const double* const* Rhat
   return mx;
 }
 
+int ttm_order(const Shape& s, int dtype, const double* const* Rhat, const int64_t* Ic, int tensor_cores, int* order) {
+  int k = 0;
+  bool shrink = true;
+  for (int n = 0; n < s.N; ++n)
+    if (Rhat[n] && Ic[n] > s.dims[n]) shrink = false;
+  if (tensor_cores && dtype == CPMG_F32 && s.N > 2 && Rhat[0] && shrink) {
+    order[k++] = 0;
+    for (int n = s.N - 1; n >= 1; --n)
+      if (Rhat[n]) order[k++] = n;
+  } else {
+    for (int n = 0; n < s.N; ++n)
+      if (Rhat[n]) order[k++] = n;
+  }
+  return k;
+}
+
 int ttm_restrict(const Shape& s, const void* Z, int dtype, const double* const* Rhat, const int64_t* Ic,
                  void* Y, void* tmp0, void* tmp1, int tensor_cores, void* tc_scratch, int* err,
                  const cudaEvent_t* ev, bool ev_external, cudaStream_t st) {
-  int last = -1;
-  for (int n = 0; n < s.N; ++n)
-    if (Rhat[n]) last = n;
-  if (last < 0) {
+  int order[kMaxModes];
+  const int k = ttm_order(s, dtype, Rhat, Ic, tensor_cores, order);
+  if (k == 0) {
     const size_t esz = dtype == CPMG_F64 ? 8 : 4;
     CPMG_CUDA_TRY(cudaMemcpyAsync(Y, Z, s.numel() * esz, cudaMemcpyDeviceToDevice, st));
     return CPMG_OK;
@@ -163,9 +178,9 @@ int ttm_restrict(const Shape& s, const void* Z, int dtype, const double* const* 
   Shape cur = s;
   const void* src = Z;
   int flip = 0;
-  for (int n = 0; n < s.N; ++n) {
-    if (!Rhat[n]) continue;
-    void* dst = (n == last) ? Y : (flip ? tmp1 : tmp0);
+  for (int j = 0; j < k; ++j) {
+    const int n = order[j];
+    void* dst = (j == k - 1) ? Y : (flip ? tmp1 : tmp0);
     CPMG_TRY(ttm_mode(cur, src, dtype, n, Rhat[n], Ic[n], dst, tensor_cores, tc_scratch, err,
                       ev ? ev[2 * n] : nullptr, ev ? ev[2 * n + 1] : nullptr, ev_external, st));
     cur.dims[n] = Ic[n];

@@ -21,6 +21,13 @@ int ttm_restrict(const Shape& s, const void* Z, int dtype, const double* const* 
                  void* Y, void* tmp0, void* tmp1, int tensor_cores, void* tc_scratch, int* err,
                  const cudaEvent_t* ev, bool ev_external, cudaStream_t st);
 
+// The order in which ttm_restrict applies the mode products (writes the modes to order[], returns
+// their count). Increasing n, except on the tensor-core float path when mode 1 is restricted and
+// no mode grows. There it is mode 1, then the last mode down to mode 2: a middle mode with few
+// rows in front of it pads its 128-row tensor-core tiles, and it then works on the smallest
+// tensor. The first intermediate, which is the largest, is the same in both orders.
+int ttm_order(const Shape& s, int dtype, const double* const* Rhat, const int64_t* Ic, int tensor_cores, int* order);
+
 // Bytes of the largest intermediate of ttm_restrict (for sizing tmp buffers).
 size_t ttm_max_intermediate(const Shape& s, int dtype, const double* const* Rhat, const int64_t* Ic);
 
