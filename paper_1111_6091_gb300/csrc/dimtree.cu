@@ -226,8 +226,200 @@ static void launch_w_rp(const TZ* X, int64_t P, int64_t K, int R, const double* 
   }
 }
 
+// ------------------------------------------------------------------ W = X C, FP32, streamed ring
+// The FP32 W pass with its loads taken off the arithmetic warps. CTA b owns the PB consecutive rows
+// p_b .. p_b + PB - 1 (PB about P / SMs, so one CTA per SM and no second wave). Column k of those
+// rows is one contiguous run of 4 PB bytes, and a producer warp streams KS such runs per stage
+// with cp.async.bulk into a ring of S stages. Consumer thread t owns rows 4t .. 4t + 3 of the block
+// and accumulates, column after column, exactly the FMAs of k_dt_w's FP32 path in the same order,
+// so both give the same bits. Every wait is bounded (about 2 s); on expiry *err is set and the
+// CTA unwinds, after the copies it issued have landed.
+constexpr int kRingStages = 4;
+constexpr int kRingCols = 8;     // columns per stage
+constexpr int kRingMaxPB = 4 * (1024 - 32);
+constexpr size_t kRingCBytes = 64 * 1024;  // C as float, K x RP, must fit
+
+__device__ __forceinline__ uint32_t ring_su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t ring_gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool ring_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(ring_su32(bar)), "r"(parity), "r"(1000000u)
+      : "memory");
+  return ok != 0;
+}
+__device__ bool ring_wait(uint64_t* bar, uint32_t parity, const int* fail) {
+  if (ring_try(bar, parity)) return true;
+  const uint64_t t0 = ring_gtime();
+  while (true) {
+    if (ring_try(bar, parity)) return true;
+    if ((fail && *reinterpret_cast<const volatile int*>(fail)) || ring_gtime() - t0 > 2000000000ull) return false;
+  }
+}
+
+template <int RP>
+__global__ void k_dt_w_ring(const float* __restrict__ X, int64_t P, int64_t K, int R, const double* __restrict__ C,
+                            double* __restrict__ W, int PB, int nc, int* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + kRingStages;
+  int* fail = reinterpret_cast<int*>(smem + 128);
+  float* cs = reinterpret_cast<float*>(smem + 256);
+  const size_t cbytes = ((size_t)K * RP * 4 + 127) & ~(size_t)127;
+  unsigned char* ring = smem + 256 + cbytes;
+  const uint32_t stage_bytes = (uint32_t)kRingCols * (uint32_t)PB * 4u;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int ncw = nc >> 5;  // consumer warps
+  const int64_t p0 = (int64_t)blockIdx.x * PB;
+  const int plen = (int)((P - p0) < PB ? (P - p0) : PB);
+  const int nst = (int)((K + kRingCols - 1) / kRingCols);
+  if (t == 0) {
+    for (int s2 = 0; s2 < kRingStages; ++s2) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(ring_su32(&full[s2])), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(ring_su32(&empty[s2])), "r"(ncw) : "memory");
+    }
+    *fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int64_t e = t; e < K * RP; e += blockDim.x) {
+    const int64_t k = e / RP;
+    const int r = (int)(e % RP);
+    cs[e] = r < R ? (float)C[k + K * r] : 0.f;
+  }
+  __syncthreads();
+  if (warp == ncw) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      int it = 0;
+      for (; it < nst; ++it) {
+        const int slot = it % kRingStages;
+        if (it >= kRingStages &&
+            !ring_wait(&empty[slot], (uint32_t)(((it / kRingStages) - 1) & 1), fail)) {
+          atomicOr(fail, 1);
+          break;
+        }
+        const int64_t k0 = (int64_t)it * kRingCols;
+        const int cols = (int)((K - k0) < kRingCols ? (K - k0) : kRingCols);
+        const uint32_t bytes = (uint32_t)plen * 4u;
+        unsigned char* st = ring + (size_t)slot * stage_bytes;
+        asm volatile("{\n\t.reg .b64 sx;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 sx, [%0], %1;\n\t}" ::"r"(
+                         ring_su32(&full[slot])),
+                     "r"(bytes * (uint32_t)cols)
+                     : "memory");
+        for (int j = 0; j < cols; ++j)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  ring_su32(st + (size_t)j * PB * 4)),
+              "l"(X + p0 + P * (k0 + j)), "r"(bytes), "r"(ring_su32(&full[slot]))
+              : "memory");
+      }
+      // copies still in flight must land before the CTA exits (only their own phase ends this)
+      for (int j = (it > kRingStages ? it - kRingStages : 0); j < it; ++j)
+        if (!ring_wait(&full[j % kRingStages], (uint32_t)((j / kRingStages) & 1), nullptr)) atomicOr(fail, 1);
+    }
+  } else {
+    // ---------------------------------------------------------------- consumers
+    const int q = 4 * t;  // first of this thread's four rows in the block
+    const bool live = q < plen;
+    float acc[4][RP];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int r = 0; r < RP; ++r) acc[v][r] = 0.f;
+    for (int it = 0; it < nst; ++it) {
+      const int slot = it % kRingStages;
+      int ok = 1;
+      if (lane == 0) ok = ring_wait(&full[slot], (uint32_t)((it / kRingStages) & 1), fail) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        if (lane == 0) atomicOr(fail, 1);
+        break;
+      }
+      __syncwarp();
+      const int64_t k0 = (int64_t)it * kRingCols;
+      const int cols = (int)((K - k0) < kRingCols ? (K - k0) : kRingCols);
+      if (live) {
+        const unsigned char* st = ring + (size_t)slot * stage_bytes + (size_t)q * 4;
+        // one column: four rows times RP coefficients, the coefficients read four at a time
+        auto column = [&](int j) {
+          const float4 x = *reinterpret_cast<const float4*>(st + (size_t)j * PB * 4);
+          const float4* c4 = reinterpret_cast<const float4*>(cs + (k0 + j) * RP);
+#pragma unroll
+          for (int r4 = 0; r4 < RP / 4; ++r4) {
+            const float4 cq = c4[r4];
+            const float cr[4] = {cq.x, cq.y, cq.z, cq.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int r = 4 * r4 + i;
+              acc[0][r] = __fmaf_rn(x.x, cr[i], acc[0][r]);
+              acc[1][r] = __fmaf_rn(x.y, cr[i], acc[1][r]);
+              acc[2][r] = __fmaf_rn(x.z, cr[i], acc[2][r]);
+              acc[3][r] = __fmaf_rn(x.w, cr[i], acc[3][r]);
+            }
+          }
+        };
+        if (cols == kRingCols) {
+#pragma unroll
+          for (int j = 0; j < kRingCols; ++j) column(j);
+        } else {
+          for (int j = 0; j < cols; ++j) column(j);
+        }
+      }
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("{\n\t.reg .b64 sx;\n\tmbarrier.arrive.shared::cta.b64 sx, [%0];\n\t}" ::"r"(
+                         ring_su32(&empty[slot]))
+                     : "memory");
+    }
+    if (live && !*reinterpret_cast<volatile int*>(fail)) {
+#pragma unroll
+      for (int r = 0; r < RP; ++r)
+        if (r < R)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) W[p0 + q + v + P * r] = (double)acc[v][r];
+    }
+  }
+  __syncthreads();
+  if (t == 0 && *fail && err) atomicOr(err, 1);
+}
+
+// launches the ring kernel when the shapes suit it; false: use k_dt_w
+static bool launch_w_ring(const float* X, int64_t P, int64_t K, int R, const double* C, double* W, int num_sms,
+                          int* err, cudaStream_t st) {
+  const int RP = R <= 4 ? 4 : R <= 8 ? 8 : R <= 12 ? 12 : 16;
+  if (P % 4 != 0 || reinterpret_cast<uintptr_t>(X) % 16 != 0 || (size_t)K * RP * 4 > kRingCBytes || num_sms < 1)
+    return false;
+  int64_t PB = ((P + num_sms - 1) / num_sms + 3) / 4 * 4;
+  if (PB < 256) return false;  // too few rows per CTA for the copies to pay
+  if (PB > kRingMaxPB) PB = kRingMaxPB;
+  const int nc = (int)((PB / 4 + 31) / 32 * 32);
+  const size_t cbytes = ((size_t)K * RP * 4 + 127) & ~(size_t)127;
+  const size_t smem = 256 + cbytes + (size_t)kRingStages * kRingCols * PB * 4;
+  int optin = 0, dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 0;
+  cudaGetLastError();
+  if (smem > (size_t)optin) return false;
+  const unsigned grid = (unsigned)((P + PB - 1) / PB);
+  const unsigned block = (unsigned)(nc + 32);
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, block, smem, st>>>(X, P, K, R, C, W, (int)PB, nc, err);
+  };
+  if (RP == 4) go(k_dt_w_ring<4>);
+  else if (RP == 8) go(k_dt_w_ring<8>);
+  else if (RP == 12) go(k_dt_w_ring<12>);
+  else go(k_dt_w_ring<16>);
+  return true;
+}
+
 int launch_dt_w(const void* X, int zdtype, int64_t P, int64_t K, int R, const double* C, int prec, double* W,
-                int num_sms, cudaStream_t st) {
+                int num_sms, cudaStream_t st, int* err) {
   if (R < 1 || R > 16 || P < 1 || K < 1) return CPMG_INVALID_ARG;
   if (zdtype == CPMG_F64 && prec == P_DF) prec = P_FP64;
   const uintptr_t xa = reinterpret_cast<uintptr_t>(X);
@@ -248,6 +440,7 @@ int launch_dt_w(const void* X, int zdtype, int64_t P, int64_t K, int R, const do
     const int vw = v2many ? 2 : fits(4, 16) ? 4 : fits(2, 8) ? 2 : 1;
     switch (prec) {
       case P_FP32:
+        if (launch_w_ring(x, P, K, R, C, W, num_sms, err, st)) break;
         vw == 4 ? launch_w_rp<float, P_FP32, 4>(x, P, K, R, C, W, st)
                 : vw == 2 ? launch_w_rp<float, P_FP32, 2>(x, P, K, R, C, W, st)
                           : launch_w_rp<float, P_FP32, 1>(x, P, K, R, C, W, st);

@@ -36,8 +36,11 @@ int launch_transpose_d(const double* src, int64_t I, int R, double* dst, cudaStr
 // float64 elements, `zdtype`) and a float64 K x R factor C, written as float64 P x R column-major.
 // prec: P_FP32 (float products and sums), P_DF (float-pair sums, float64-accurate), P_FP64.  One
 // pass over X with no partial sums: every thread owns whole rows and walks all K columns, with C
-// staged in shared memory.  Returns CPMG_INVALID_ARG for R outside 1..16.
+// staged in shared memory.  FP32 on float X, when the rows split into blocks of 256 or more per SM,
+// streams each block's columns through a ring of bulk copies instead (same arithmetic, same bits);
+// *err (may be null) receives 1 if one of its bounded waits expired.  Returns CPMG_INVALID_ARG for R
+// outside 1..16.
 int launch_dt_w(const void* X, int zdtype, int64_t P, int64_t K, int R, const double* C, int prec, double* W,
-                int num_sms, cudaStream_t st);
+                int num_sms, cudaStream_t st, int* err = nullptr);
 
 }  // namespace cpmg

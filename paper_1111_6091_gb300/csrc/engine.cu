@@ -581,7 +581,7 @@ static int dt_form_w(Solver& S, const Level& L, const FactorSet& f, int prec) {
     CPMG_TRY(prof_events(c, eff == P_FP32 ? 0 : (eff == P_DF ? 1 : 2), bytes, &e0, &e1));
   }
   if (e0) CPMG_CUDA_TRY(cudaEventRecordWithFlags(e0, S.st, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
-  CPMG_TRY(launch_dt_w(L.Z, L.dtype, P, K, f.R, f.A[2], prec, L.W, c->num_sms, S.st));
+  CPMG_TRY(launch_dt_w(L.Z, L.dtype, P, K, f.R, f.A[2], prec, L.W, c->num_sms, S.st, c->dstatus + 1));
   if (e1) CPMG_CUDA_TRY(cudaEventRecordWithFlags(e1, S.st, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   c->launches += 1;
   return CPMG_OK;

@@ -333,11 +333,14 @@ def test_split_bf16_sweeps_match_oracle(cpmg_ctx):
     assert_same_stationary_point(Z64, host(cpmg, A), ref_c, 1e-10)
 
 
-def test_dimension_tree_w_pass_large_fp32(cpmg_ctx):
-    """A tensor with enough rows (400 x 400 x 64) for the W pass's four-rows-per-thread, packed-FMA
-    variant: one FP32 sweep with the tree matches the sweep without it and the oracle's ALS."""
+@pytest.mark.parametrize("dims,R", [((400, 400, 64), 10), ((200, 300, 37), 7)])
+def test_dimension_tree_w_pass_large_fp32(cpmg_ctx, dims, R):
+    """Tensors with enough rows for the FP32 W pass's streamed ring: at least 256 rows per SM, each
+    CTA's rows read column by column through bulk copies. The second shape leaves a short last block
+    of rows (60 000 rows in blocks of 396) and a short last stage of columns (37 = 4 x 8 + 5). One
+    FP32 sweep with the tree matches the sweep without it, and the oracle's ALS."""
     from paper_1111_6091_gb300 import cpmg
-    p = synth.make_problem((400, 400, 64), 10, congruence=0.5, eta_homo=0.01, dtype=np.float32, seed=8, n_t=0)
+    p = synth.make_problem(dims, R, congruence=0.5, eta_homo=0.01, dtype=np.float32, seed=8, n_t=0)
     Z64 = p.Z.astype(np.float64)
     ref = ALS.sort_components(ALS.als_sweep(Z64, p.A0))
     out = []
