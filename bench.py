@@ -840,7 +840,7 @@ def run_sweep_case(args):
 
 def run_batch_case(args):
     """Profiler case: the 512-tensor batch workload, 8 MIXED sweeps of every tensor plus one g
-    evaluation.  Launches: the unit-size autotuner (5 candidates x (k_batch_init + 2 MTTKRP-only
+    evaluation.  Launches: the unit-size autotuner (5 candidates x (k_batch_init + 3 MTTKRP-only
     k_batch)), then one k_batch of 8 sweeps + g, then k_batch_sort."""
     import torch
     from paper_1111_6091_gb300 import cpmg
