@@ -195,3 +195,27 @@ def test_fas_operator_equals_gradient():
     A = rand_factors(dims, 2, 19)
     for n in range(3):
         assert np.allclose(T.fas_operator(Z, A, n), T.gradient(Z, A, n))
+
+
+@pytest.mark.parametrize("dims", [(5, 4, 6), (4, 3, 5, 2)])
+def test_mode_products_commute(dims):
+    """The restriction's mode products commute (Section 2: x_m and x_n act on different indices):
+    applying them in increasing order, or mode 1 first and then the last mode down to mode 2 (the
+    order the tensor-core path uses), gives the full contraction with every matrix, written out
+    with einsum."""
+    Z = rand_tensor(dims, 11)
+    rng = np.random.default_rng(12)
+    Ms = [rng.standard_normal(((I + 1) // 2, I)) for I in dims]
+    N = len(dims)
+    inc = Z
+    for n in range(N):
+        inc = T.ttm(inc, Ms[n], n)
+    alt = T.ttm(Z, Ms[0], 0)
+    for n in range(N - 1, 0, -1):
+        alt = T.ttm(alt, Ms[n], n)
+    letters = "abcd"[:N]
+    spec = letters + "," + ",".join("%s%s" % (c.upper(), c) for c in letters) + "->" + letters.upper()
+    ref = np.einsum(spec, Z, *Ms)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(inc - ref)) <= 1e-12 * scale
+    assert np.max(np.abs(alt - ref)) <= 1e-12 * scale
